@@ -1,0 +1,106 @@
+"""The pins have teeth: plausible mistakes planted in copies of the oracle
+(a dropped term, a wrong sign, a swapped operand, an off-by-one bound, a wrong
+divisor) each make at least one pin fail.  Everything here runs on the CPU;
+the real oracle is restored after every mutant."""
+import os
+import subprocess
+
+import pytest
+
+import oracle as O
+from tests import test_oracle_algorithms as TA
+from tests import test_oracle_applications as TP
+from tests import test_oracle_horner_ew as TH
+from tests import test_oracle_reduce as TR
+from tests import test_oracle_transforms as TT
+
+SRC = os.path.join(os.path.dirname(O.__file__), "twofold_oracle.c")
+
+
+def _in_function(src, fname, old, new):
+    """Replace the first `old` inside the body of C function `fname`."""
+    start = src.index(fname + "(")
+    brace = src.index("{", start)
+    depth, i = 0, brace
+    while True:
+        if src[i] == "{":
+            depth += 1
+        elif src[i] == "}":
+            depth -= 1
+            if depth == 0:
+                break
+        i += 1
+    body = src[brace:i]
+    assert old in body, (fname, old)
+    return src[:brace] + body.replace(old, new, 1) + src[i:]
+
+
+DATA = None
+
+
+def data():
+    global DATA
+    if DATA is None:
+        DATA = TA.make_data()
+    return DATA
+
+
+MUTANTS = {
+    "mtf1_drops_p11": (("tfo_mtf1", "double u = e00 + p11;", "double u = e00;"),
+                       [lambda: TA.test_mtf1_budget(data())]),
+    "two_diff_printed_signs": (("tfo_two_diff", "double bs = b1 - b;", "double bs = b - b1;"),
+                               [lambda: TT.test_two_diff_exact(TT.make_pairs())]),
+    "atf1_subtracts_tail": (("tfo_atf1", "double u = x1 + y1;", "double u = x1 - y1;"),
+                            [lambda: TA.test_atf1_budget(data())]),
+    "dtf1_divides_by_y0": (("tfo_dtf1", "z.z1 = c0 / d0;", "z.z1 = c0 / y0;"),
+                           [lambda: TA.test_dtf1_budget(data())]),
+    "dtf1_r1_sign": (("tfo_dtf1", "fma(-q, y1, x1)", "fma(q, y1, x1)"),
+                     [lambda: TA.test_dtf1_budget(data())]),
+    "rpf11_no_factor_two": (("tfo_rpf11", "double w = 2.0 * c;", "double w = c;"),
+                            [lambda: TA.test_rpf11_output_coupled(data())]),
+    "rtf1_drops_u1": (("tfo_rtf1", "tfo_rpf1(u0, u1)", "tfo_rpf1(u0, 0.0)"),
+                      [lambda: TA.test_rtf1_coupled_loose(data())]),
+    "two_sum_swaps_roles": (("tfo_two_sum", "double b1 = s_ - a;", "double b1 = s_ - b;"),
+                            [lambda: TT.test_two_sum_exact(TT.make_pairs())]),
+    "leaf_skips_first": (("leaf_reduce", "for (int64_t i = b; i < e; ++i)",
+                          "for (int64_t i = b + 1; i < e; ++i)"),
+                         [lambda: TR.test_dot_z0_is_plain_order(1000, 256)]),
+    "tree_drops_odd_carry": (("tree_reduce", "if (m & 1) nodes[h++] = nodes[m - 1];", ""),
+                             [lambda: TR.test_sum_z0_is_plain_order(4097, 256)]),
+    "horner_stops_early": (("tfo_horner", "for (int i = k - 1; i >= 0; --i)",
+                            "for (int i = k - 1; i >= 1; --i)"),
+                           [lambda: TH.test_horner_binomial(5)]),
+    "flag_ge": (("tfo_flag", "if (fabs(z1) > lim)", "if (fabs(z1) >= lim)"),
+                [TA.test_flag_rel_and_nonfinite]),
+    "mtf11_uses_x0": (("tfo_mtf11", "double p10 = x1 * y0;", "double p10 = x0 * y0;"),
+                      [lambda: TA.test_atf11_strict(data()),
+                       lambda: TH.test_horner_binomial(10)]),
+    "stf11_adds_instead": (("tfo_stf11", "tfo_two_diff(x0, y0, &d, &e);",
+                            "tfo_two_sum(x0, y0, &d, &e);"),
+                           [lambda: TA.test_stf11_strict(data())]),
+    "gauss_dtf1_drops_d0": (("tfo_dtf1", "double d0 = y0 + y1;", "double d0 = y0 + y0;"),
+                            [lambda: TP.test_gauss_logs("gauss_well3", 0.1, (11.0, 11.0, 1.0)),
+                             lambda: TA.test_dtf1_budget(data())]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    (fname, old, new), checks = MUTANTS[name]
+    src = _in_function(open(SRC).read(), fname, old, new)
+    c = tmp_path / "mutant.c"
+    c.write_text(src)
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", *O.CFLAGS, str(c), "-o", str(so), "-lm"])
+    saved = O.lib()
+    O._lib = O.load(str(so))
+    failed = 0
+    try:
+        for chk in checks:
+            try:
+                chk()
+            except AssertionError:
+                failed += 1
+    finally:
+        O._lib = saved
+    assert failed > 0, f"mutant {name} survived the pins"
