@@ -1,0 +1,227 @@
+/*
+ * twofold.h -- C ABI of the GB300 twofold library.
+ *
+ * Twofold fast arithmetic (E. Latkin, "Twofold fast arithmetic",
+ * arXiv:1401.6235): a value z is carried as z ~ z0 + z1 where z0 is bit for
+ * bit the plain IEEE binary64 result of the same computation and z1
+ * estimates its error dz0 = z - z0 (Algorithms, "Methodic").  Every entry
+ * point below returns, per result, z0, z1 and a panic flag byte.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ *  - Arrays are structure-of-arrays: a twofold array is a pair of binary64
+ *    arrays `hi` (z0) and `lo` (z1).  `lo == NULL` marks a "dotted" input: a
+ *    plain binary64 value with no tail, which selects the paper's ".1"
+ *    algorithms (see twofold_ew for the exact rule).
+ *  - Unless stated otherwise, data pointers are DEVICE pointers owned by the
+ *    caller (for example torch tensors); the library never allocates, frees
+ *    or synchronises.  Every call is asynchronous on `stream` (a
+ *    cudaStream_t passed as void*; NULL is the legacy default stream).
+ *  - Device data pointers must be 8-byte aligned (flags: any alignment).
+ *    Lengths are element counts; n == 0 is valid.
+ *  - Results are deterministic and independent of launch configuration:
+ *    z0, z1 and flags are bit-identical to the CPU oracle of the same
+ *    operation order (NaN payloads excepted).
+ *  - NaN and Inf are not errors (Algorithms, "Methodic": no special-case
+ *    processing); they propagate through the basic operations and raise
+ *    TF_FLAG_NONFINITE.
+ *  - Return value: TF_OK or a negative tf_status.  Argument errors are
+ *    detected before any launch (nothing is written); TF_ECUDA reports a
+ *    launch error (cudaGetLastError) and leaves outputs undefined.
+ *  - Compiled with -fmad=false and explicit round-to-nearest intrinsics:
+ *    no multiply-add is contracted, so z0 is the plain IEEE result.
+ */
+#ifndef TWOFOLD_H
+#define TWOFOLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- types */
+
+/* A twofold input array: hi = z0 values; lo = z1 tails, or NULL (dotted). */
+typedef struct {
+    const double *hi;
+    const double *lo;
+} tf_in;
+
+/* A twofold output array.  hi and lo are required (n doubles each, or one
+ * per job for reductions); flags is optional (NULL: not written). */
+typedef struct {
+    double *hi;
+    double *lo;
+    uint8_t *flags;
+} tf_out;
+
+/* Panic flag (Motivation: the "twofold daemon" that signals when z1 gets
+ * large compared with z0; the paper fixes no threshold):
+ *   TF_PANIC_REL: PANIC when |z1| > panic_tau * |z0|   (default tau = 2^-40)
+ *   TF_PANIC_ULP: PANIC when |z1| > panic_ulps * ulp(z0),
+ *                 ulp(v) = 2^(max(e,-1022)-52) for v = 1.f * 2^e, ulp(0) = 2^-1074
+ * Both products are single round-to-nearest multiplications.  NaN compares
+ * false, so a NaN z1 never raises PANIC; NONFINITE covers it. */
+enum { TF_PANIC_REL = 0, TF_PANIC_ULP = 1 };
+enum { TF_FLAG_PANIC = 1, TF_FLAG_NONFINITE = 2 };
+
+typedef struct {
+    int32_t panic_mode;   /* TF_PANIC_REL or TF_PANIC_ULP                      */
+    int32_t leaf;         /* leaf length L of sum/dot (>= 1); default 256      */
+    double  panic_tau;    /* REL threshold, default 0x1p-40                    */
+    double  panic_ulps;   /* ULP threshold m, default 4096                     */
+} tf_params;              /* a NULL tf_params* means all defaults              */
+
+typedef enum {
+    TF_OK = 0,
+    TF_EINVAL = -1,        /* bad argument (NULL, misaligned, n < 0, bad program, ...) */
+    TF_ENOSPC = -2,        /* workspace too small                                     */
+    TF_ECUDA = -3,         /* CUDA launch / runtime error                             */
+    TF_ETIMEOUT = -4,      /* a bounded device-side wait gave up                      */
+    TF_EUNSUPPORTED = -5   /* valid request outside this build's limits               */
+} tf_status;
+
+/* Human-readable text of a status code (static storage). */
+const char *twofold_strerror(int status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int twofold_version(void);
+
+/* --------------------------------------------------- elementwise programs
+ *
+ * twofold_ew -- evaluate a straight-line program over n twofold elements.
+ *
+ * Operations (Algorithms section):
+ *   TF_ADD  Add/subtract, Algorithm ATF 1  (ATF 1.1 when b is dotted)
+ *   TF_SUB  Add/subtract, Algorithm STF 1  (STF 1.1 when b is dotted)
+ *   TF_MUL  Multiply,     Algorithm MTF 1  (MTF 1.1 when b is dotted)
+ *   TF_DIV  Divide,       Algorithm DTF 1  (DTF 1.1 when b is dotted)
+ *   TF_SQRT Root,         Algorithm RTF 1  (RPF 1.1 when a is dotted)
+ * with err() of sums and differences from Algorithms 1.2 / 2.2, products
+ * from Algorithm 3, remainders from Algorithms 4 and 5 (Background).
+ * Operand kinds: both twofold -> the general algorithm; a twofold, b dotted
+ * -> the ".1" algorithm; a dotted, b twofold -> the general algorithm with
+ * a's tail = +0; both dotted -> the exact transform (Two-Sum, Two-Diff,
+ * Two-Product) or DTF 1.1.1.  Only inputs can be dotted; every
+ * intermediate is a general twofold.
+ *
+ * prog    HOST array of nprog instructions, 4 int32 each: {op, dst, a, b}.
+ *         Registers 0..nin-1 are the inputs (read only); registers
+ *         nin..TF_EW_MAX_REGS-1 are temporaries.  a and b must name an input
+ *         or a temporary written by an earlier instruction; b is ignored
+ *         for TF_SQRT.  The result is the last instruction's dst.
+ * nprog   1..TF_EW_MAX_PROG.
+ * in      HOST array of nin tf_in descriptors (device data pointers).
+ * nin     1..TF_EW_MAX_INPUTS.
+ * n       elements (>= 0); every input and output array holds n values.
+ * out     z0, z1 (n doubles each) and optional flags (n bytes).
+ * p       panic parameters (NULL: defaults).
+ * Errors: TF_EINVAL for a malformed program or bad pointers.
+ */
+enum { TF_ADD = 1, TF_SUB = 2, TF_MUL = 3, TF_DIV = 4, TF_SQRT = 5 };
+enum { TF_EW_MAX_PROG = 32, TF_EW_MAX_INPUTS = 12, TF_EW_MAX_REGS = 32 };
+
+int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, int32_t nin,
+               int64_t n, tf_out out, const tf_params *p, void *stream);
+
+/* Plain binary64 twin of twofold_ew: the same program on the hi arrays
+ * only (in: HOST array of nin device pointers), out[i] = the plain result.
+ * It equals twofold_ew's z0 bit for bit. */
+int plain_ew(const int32_t *prog, int32_t nprog, const double *const *in, int32_t nin,
+             int64_t n, double *out, void *stream);
+
+/* ------------------------------------------------------ sum and dot
+ *
+ * Reduction order (the paper fixes none; "2x" section: a twofold
+ * accumulator summing plain values is strict per step, Algorithm ATF 1.1):
+ *   - leaves are consecutive blocks of L = p->leaf elements (the last may
+ *     be short); each leaf runs acc = (+0, +0), acc = ATF1(acc, term_i)
+ *     from left to right, where term_i is x_i (ATF 1.1 when x is dotted)
+ *     for a sum, or the twofold product of x_i and y_i for a dot (Two-
+ *     Product when both are dotted, MTF 1 when both are twofold, MTF 1.1
+ *     when only y is dotted, MTF 1 with x1 = +0 when only x is dotted);
+ *   - the leaf results are combined by a bottom-up pairwise tree: node i
+ *     of level j+1 = ATF1(node 2i, node 2i+1) of level j, an odd last node
+ *     is carried up unchanged; the root is the result (n = 0: (+0, +0)).
+ * Node i of level j covers leaves [i 2^j, min((i+1) 2^j, m)), so any
+ * aligned 2^k-leaf block is a subtree: the GPU reduces blocks in parallel
+ * and combines their partials in the same order.
+ *
+ * out1    one result: out1.hi[0], out1.lo[0], out1.flags[0] (optional).
+ * ws      DEVICE workspace of ws_bytes >= twofold_workspace_bytes(...);
+ *         its contents on entry are irrelevant; it is scratch until the
+ *         stream reaches the end of the call.
+ * Errors: TF_ENOSPC if ws_bytes is too small.
+ */
+enum { TF_KIND_SUM = 1, TF_KIND_DOT = 2 };
+
+size_t twofold_workspace_bytes(int32_t kind, int64_t n_total, int32_t njobs,
+                               const tf_params *p);
+
+int twofold_sum(tf_in x, int64_t n, tf_out out1, const tf_params *p,
+                void *ws, size_t ws_bytes, void *stream);
+int twofold_dot(tf_in x, tf_in y, int64_t n, tf_out out1, const tf_params *p,
+                void *ws, size_t ws_bytes, void *stream);
+
+/* Batched (one launch for all jobs): job j reduces elements
+ * [offs[j], offs[j+1]) of x (and y) and writes out.hi[j], out.lo[j],
+ * out.flags[j].  offs is a HOST array of njobs+1 non-decreasing int64 with
+ * offs[0] >= 0; the job table derived from it is uploaded into ws with
+ * cudaMemcpyAsync (the call returns once the host array may be reused).
+ * Jobs of any lengths may be mixed; each result equals the single-job call. */
+int twofold_sum_batched(tf_in x, const int64_t *offs, int32_t njobs, tf_out out,
+                        const tf_params *p, void *ws, size_t ws_bytes, void *stream);
+int twofold_dot_batched(tf_in x, tf_in y, const int64_t *offs, int32_t njobs, tf_out out,
+                        const tf_params *p, void *ws, size_t ws_bytes, void *stream);
+
+/* Plain binary64 twins: the same leaves and tree with s = +0; s = s (+) x_i
+ * (sum) or s = s (+) (x_i (*) y_i) (dot, separate multiply and add).  They
+ * equal the twofold z0 bit for bit.  out: one double per job (device). */
+int plain_sum(const double *x, int64_t n, double *out1, const tf_params *p,
+              void *ws, size_t ws_bytes, void *stream);
+int plain_dot(const double *x, const double *y, int64_t n, double *out1, const tf_params *p,
+              void *ws, size_t ws_bytes, void *stream);
+int plain_dot_batched(const double *x, const double *y, const int64_t *offs, int32_t njobs,
+                      double *out, const tf_params *p, void *ws, size_t ws_bytes, void *stream);
+
+/* -------------------------------------------------------------- Horner
+ *
+ * p(x) = a_0 + a_1 x + ... + a_k x^k with dotted coefficients (ascending)
+ * and dotted points: s = (a_k, +0); for i = k-1 .. 0:
+ *     s = ATF 1.1( MTF 1.1(s, x), a_i )
+ * (Multiply: MTF 1.1; Add/subtract: ATF 1.1; the composition is not in the
+ * paper).  One result per point.
+ *
+ * coef    DEVICE array of k+1 doubles, a_0 first.  0 <= k <= TF_HORNER_MAX_K.
+ * x       DEVICE array of n points; out: n results.
+ */
+enum { TF_HORNER_MAX_K = 1024 };
+
+int twofold_horner(const double *coef, int32_t k, const double *x, int64_t n, tf_out out,
+                   const tf_params *p, void *stream);
+
+/* Batched: job j evaluates the degree-ks[j] polynomial with coefficients
+ * coefs[coef_offs[j] .. coef_offs[j] + ks[j]] at points
+ * x[x_offs[j] .. x_offs[j+1]), writing out at the same indices.
+ * coefs and x are DEVICE arrays; coef_offs, ks (njobs each) and x_offs
+ * (njobs+1, non-decreasing, x_offs[0] >= 0) are HOST arrays, uploaded into
+ * ws (ws_bytes >= twofold_horner_workspace_bytes(njobs)). */
+size_t twofold_horner_workspace_bytes(int32_t njobs);
+int twofold_horner_batched(const double *coefs, const int32_t *coef_offs, const int32_t *ks,
+                           int32_t njobs, const double *x, const int64_t *x_offs, tf_out out,
+                           const tf_params *p, void *ws, size_t ws_bytes, void *stream);
+
+/* Plain twins: s = a_k; s = (s (*) x) (+) a_i, no FMA. */
+int plain_horner(const double *coef, int32_t k, const double *x, int64_t n, double *out,
+                 void *stream);
+int plain_horner_batched(const double *coefs, const int32_t *coef_offs, const int32_t *ks,
+                         int32_t njobs, const double *x, const int64_t *x_offs, double *out,
+                         void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TWOFOLD_H */

@@ -1,0 +1,329 @@
+"""GB300 twofold arithmetic: Python binding of libtwofold.so.
+
+Twofold fast arithmetic (Latkin, arXiv:1401.6235) carries z ~ z0 + z1: z0 is
+the plain IEEE binary64 result, z1 estimates its error, and a per-result
+flag byte signals when z1 is large relative to z0.  All arithmetic runs in
+the CUDA kernels of ``libtwofold.so`` (C ABI declared in include/twofold.h);
+this module only marshals torch tensors (device memory, streams) into
+pointers and sizes.  There is no CPU fallback: importing works without a
+GPU, but every call needs the built library and CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtwofold.so")
+
+TF_OK, TF_EINVAL, TF_ENOSPC, TF_ECUDA, TF_ETIMEOUT, TF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+ADD, SUB, MUL, DIV, SQRT = 1, 2, 3, 4, 5
+PANIC, NONFINITE = 1, 2
+PANIC_REL, PANIC_ULP = 0, 1
+KIND_SUM, KIND_DOT = 1, 2
+MAX_PROG, MAX_INPUTS, MAX_REGS = 32, 12, 32
+
+#: the elementwise chain z = sqrt((a*b + c)/d) over inputs a, b, c, d (registers 0..3)
+CHAIN_SQRT_MAD_DIV = [(MUL, 4, 0, 1), (ADD, 5, 4, 2), (DIV, 6, 5, 3), (SQRT, 7, 6, 6)]
+
+
+class TwofoldError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+class tf_in(ctypes.Structure):
+    _fields_ = [("hi", ctypes.c_void_p), ("lo", ctypes.c_void_p)]
+
+
+class tf_out(ctypes.Structure):
+    _fields_ = [("hi", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("flags", ctypes.c_void_p)]
+
+
+class tf_params(ctypes.Structure):
+    _fields_ = [("panic_mode", ctypes.c_int32), ("leaf", ctypes.c_int32),
+                ("panic_tau", ctypes.c_double), ("panic_ulps", ctypes.c_double)]
+
+
+def params(panic_mode: int = PANIC_REL, leaf: int = 256, panic_tau: float = 2.0 ** -40,
+           panic_ulps: float = 4096.0) -> tf_params:
+    return tf_params(panic_mode, leaf, panic_tau, panic_ulps)
+
+
+# Every symbol the header declares, with its ctypes signature.
+_P, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_IN, _OUT, _PP = tf_in, tf_out, ctypes.POINTER(tf_params)
+SIGNATURES = {
+    "twofold_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "twofold_version": ([], ctypes.c_int),
+    "twofold_ew": ([_P, _I32, _P, _I32, _I64, _OUT, _PP, _P], ctypes.c_int),
+    "plain_ew": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
+    "twofold_workspace_bytes": ([_I32, _I64, _I32, _PP], _SZ),
+    "twofold_sum": ([_IN, _I64, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
+    "twofold_dot": ([_IN, _IN, _I64, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
+    "twofold_sum_batched": ([_IN, _P, _I32, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
+    "twofold_dot_batched": ([_IN, _IN, _P, _I32, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
+    "plain_sum": ([_P, _I64, _P, _PP, _P, _SZ, _P], ctypes.c_int),
+    "plain_dot": ([_P, _P, _I64, _P, _PP, _P, _SZ, _P], ctypes.c_int),
+    "plain_dot_batched": ([_P, _P, _P, _I32, _P, _PP, _P, _SZ, _P], ctypes.c_int),
+    "twofold_horner": ([_P, _I32, _P, _I64, _OUT, _PP, _P], ctypes.c_int),
+    "twofold_horner_workspace_bytes": ([_I32], _SZ),
+    "twofold_horner_batched": ([_P, _P, _P, _I32, _P, _P, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
+    "plain_horner": ([_P, _I32, _P, _I64, _P, _P], ctypes.c_int),
+    "plain_horner_batched": ([_P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library.  Raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run __graft_entry__.build() "
+                               "(the twofold path has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().twofold_strerror(status).decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != TF_OK:
+        raise TwofoldError(status, where)
+
+
+# ------------------------------------------------------------ marshalling
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(t, name="tensor"):
+    """Device pointer of a contiguous CUDA float64/uint8 tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the twofold path has no CPU fallback)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _pp(p):
+    return None if p is None else ctypes.byref(p)
+
+
+_ws_cache = {}
+
+
+def workspace(nbytes: int, device=None):
+    """A cached uint8 CUDA workspace of at least nbytes (grown on demand).
+    Calls on one stream may share it; concurrent streams need their own."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    buf = _ws_cache.get(dev)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 1 << 16), dtype=torch.uint8, device=dev)
+        _ws_cache[dev] = buf
+    return buf
+
+
+def _outputs(n, device, out):
+    torch = _torch()
+    if out is not None:
+        return out
+    return (torch.empty(n, dtype=torch.float64, device=device),
+            torch.empty(n, dtype=torch.float64, device=device),
+            torch.empty(n, dtype=torch.uint8, device=device))
+
+
+def _prog_array(prog):
+    a = np.ascontiguousarray(np.asarray(prog, np.int32).reshape(-1, 4))
+    return a
+
+
+# ------------------------------------------------------------ entry points
+
+def twofold_ew(prog, inputs, out=None, p: tf_params | None = None, stream=None):
+    """Evaluate program ``prog`` (rows (op, dst, a, b)) over twofold inputs.
+
+    inputs: list of (hi, lo) CUDA float64 tensors, lo None for dotted input.
+    Returns (z0, z1, flags) tensors (or fills ``out``)."""
+    pa = _prog_array(prog)
+    n = inputs[0][0].numel()
+    ins = (tf_in * len(inputs))(*[tf_in(_dev(h, "hi"), _dev(lo, "lo")) for h, lo in inputs])
+    for h, lo in inputs:
+        if h.numel() != n or (lo is not None and lo.numel() != n):
+            raise ValueError("inputs must all have the same length")
+    hi, lo_, fl = _outputs(n, inputs[0][0].device, out)
+    o = tf_out(_dev(hi), _dev(lo_), _dev(fl))
+    _check(lib().twofold_ew(pa.ctypes.data, pa.shape[0], ins, len(inputs), n, o, _pp(p),
+                            _stream(stream)), "twofold_ew")
+    return hi, lo_, fl
+
+
+def plain_ew(prog, his, out=None, stream=None):
+    torch = _torch()
+    pa = _prog_array(prog)
+    n = his[0].numel()
+    ptrs = (ctypes.c_void_p * len(his))(*[_dev(h) for h in his])
+    out = torch.empty(n, dtype=torch.float64, device=his[0].device) if out is None else out
+    _check(lib().plain_ew(pa.ctypes.data, pa.shape[0], ptrs, len(his), n, _dev(out),
+                          _stream(stream)), "plain_ew")
+    return out
+
+
+def _red_out(njobs, device, out):
+    return _outputs(njobs, device, out)
+
+
+def twofold_sum(x, xl=None, out=None, p: tf_params | None = None, ws=None, stream=None):
+    """Twofold sum in the blocked pairwise order; returns (z0, z1, flags),
+    each a 1-element CUDA tensor."""
+    n = x.numel()
+    nb = lib().twofold_workspace_bytes(KIND_SUM, n, 1, _pp(p))
+    ws = workspace(nb) if ws is None else ws
+    hi, lo, fl = _red_out(1, x.device, out)
+    _check(lib().twofold_sum(tf_in(_dev(x), _dev(xl)), n, tf_out(_dev(hi), _dev(lo), _dev(fl)),
+                             _pp(p), _dev(ws), ws.numel(), _stream(stream)), "twofold_sum")
+    return hi, lo, fl
+
+
+def twofold_dot(x, y, xl=None, yl=None, out=None, p: tf_params | None = None, ws=None, stream=None):
+    n = x.numel()
+    if y.numel() != n:
+        raise ValueError("x and y must have the same length")
+    nb = lib().twofold_workspace_bytes(KIND_DOT, n, 1, _pp(p))
+    ws = workspace(nb) if ws is None else ws
+    hi, lo, fl = _red_out(1, x.device, out)
+    _check(lib().twofold_dot(tf_in(_dev(x), _dev(xl)), tf_in(_dev(y), _dev(yl)), n,
+                             tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws), ws.numel(),
+                             _stream(stream)), "twofold_dot")
+    return hi, lo, fl
+
+
+def _offs(offs):
+    a = np.ascontiguousarray(np.asarray(offs, np.int64))
+    return a, a.size - 1
+
+
+def twofold_sum_batched(x, offs, xl=None, out=None, p: tf_params | None = None, ws=None, stream=None):
+    oa, nj = _offs(offs)
+    nb = lib().twofold_workspace_bytes(KIND_SUM, int(oa[-1]), nj, _pp(p))
+    ws = workspace(nb) if ws is None else ws
+    hi, lo, fl = _red_out(nj, x.device, out)
+    _check(lib().twofold_sum_batched(tf_in(_dev(x), _dev(xl)), oa.ctypes.data, nj,
+                                     tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws), ws.numel(),
+                                     _stream(stream)), "twofold_sum_batched")
+    return hi, lo, fl
+
+
+def twofold_dot_batched(x, y, offs, xl=None, yl=None, out=None, p: tf_params | None = None, ws=None,
+                        stream=None):
+    oa, nj = _offs(offs)
+    nb = lib().twofold_workspace_bytes(KIND_DOT, int(oa[-1]), nj, _pp(p))
+    ws = workspace(nb) if ws is None else ws
+    hi, lo, fl = _red_out(nj, x.device, out)
+    _check(lib().twofold_dot_batched(tf_in(_dev(x), _dev(xl)), tf_in(_dev(y), _dev(yl)), oa.ctypes.data,
+                                     nj, tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws),
+                                     ws.numel(), _stream(stream)), "twofold_dot_batched")
+    return hi, lo, fl
+
+
+def plain_sum(x, out=None, p: tf_params | None = None, ws=None, stream=None):
+    torch = _torch()
+    n = x.numel()
+    ws = workspace(lib().twofold_workspace_bytes(KIND_SUM, n, 1, _pp(p))) if ws is None else ws
+    out = torch.empty(1, dtype=torch.float64, device=x.device) if out is None else out
+    _check(lib().plain_sum(_dev(x), n, _dev(out), _pp(p), _dev(ws), ws.numel(), _stream(stream)),
+           "plain_sum")
+    return out
+
+
+def plain_dot(x, y, out=None, p: tf_params | None = None, ws=None, stream=None):
+    torch = _torch()
+    n = x.numel()
+    ws = workspace(lib().twofold_workspace_bytes(KIND_DOT, n, 1, _pp(p))) if ws is None else ws
+    out = torch.empty(1, dtype=torch.float64, device=x.device) if out is None else out
+    _check(lib().plain_dot(_dev(x), _dev(y), n, _dev(out), _pp(p), _dev(ws), ws.numel(),
+                           _stream(stream)), "plain_dot")
+    return out
+
+
+def plain_dot_batched(x, y, offs, out=None, p: tf_params | None = None, ws=None, stream=None):
+    torch = _torch()
+    oa, nj = _offs(offs)
+    ws = workspace(lib().twofold_workspace_bytes(KIND_DOT, int(oa[-1]), nj, _pp(p))) if ws is None else ws
+    out = torch.empty(nj, dtype=torch.float64, device=x.device) if out is None else out
+    _check(lib().plain_dot_batched(_dev(x), _dev(y), oa.ctypes.data, nj, _dev(out), _pp(p), _dev(ws),
+                                   ws.numel(), _stream(stream)), "plain_dot_batched")
+    return out
+
+
+def twofold_horner(coef, x, out=None, p: tf_params | None = None, stream=None):
+    """Twofold Horner of ascending dotted coefficients ``coef`` (CUDA float64,
+    k+1 values) at points ``x``; returns (z0, z1, flags)."""
+    n = x.numel()
+    hi, lo, fl = _outputs(n, x.device, out)
+    _check(lib().twofold_horner(_dev(coef), coef.numel() - 1, _dev(x), n,
+                                tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _stream(stream)),
+           "twofold_horner")
+    return hi, lo, fl
+
+
+def twofold_horner_batched(coefs, coef_offs, ks, x, x_offs, out=None, p: tf_params | None = None,
+                           ws=None, stream=None):
+    co = np.ascontiguousarray(np.asarray(coef_offs, np.int32))
+    kk = np.ascontiguousarray(np.asarray(ks, np.int32))
+    xo = np.ascontiguousarray(np.asarray(x_offs, np.int64))
+    nj = kk.size
+    ws = workspace(lib().twofold_horner_workspace_bytes(nj)) if ws is None else ws
+    hi, lo, fl = _outputs(x.numel(), x.device, out)
+    _check(lib().twofold_horner_batched(_dev(coefs), co.ctypes.data, kk.ctypes.data, nj, _dev(x),
+                                        xo.ctypes.data, tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p),
+                                        _dev(ws), ws.numel(), _stream(stream)), "twofold_horner_batched")
+    return hi, lo, fl
+
+
+def plain_horner(coef, x, out=None, stream=None):
+    torch = _torch()
+    out = torch.empty(x.numel(), dtype=torch.float64, device=x.device) if out is None else out
+    _check(lib().plain_horner(_dev(coef), coef.numel() - 1, _dev(x), x.numel(), _dev(out),
+                              _stream(stream)), "plain_horner")
+    return out
+
+
+def plain_horner_batched(coefs, coef_offs, ks, x, x_offs, out=None, ws=None, stream=None):
+    torch = _torch()
+    co = np.ascontiguousarray(np.asarray(coef_offs, np.int32))
+    kk = np.ascontiguousarray(np.asarray(ks, np.int32))
+    xo = np.ascontiguousarray(np.asarray(x_offs, np.int64))
+    nj = kk.size
+    ws = workspace(lib().twofold_horner_workspace_bytes(nj)) if ws is None else ws
+    out = torch.empty(x.numel(), dtype=torch.float64, device=x.device) if out is None else out
+    _check(lib().plain_horner_batched(_dev(coefs), co.ctypes.data, kk.ctypes.data, nj, _dev(x),
+                                      xo.ctypes.data, _dev(out), _dev(ws), ws.numel(), _stream(stream)),
+           "plain_horner_batched")
+    return out

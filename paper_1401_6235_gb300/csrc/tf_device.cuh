@@ -1,0 +1,232 @@
+// Device-side twofold arithmetic (Latkin, "Twofold fast arithmetic").
+//
+// Every binary64 operation is an explicit round-to-nearest intrinsic
+// (__dadd_rn, __dsub_rn, __dmul_rn, __fma_rn, __ddiv_rn, __dsqrt_rn), which
+// the compiler never contracts or reassociates; the library is also built
+// with -fmad=false.  Each function performs the operations of its algorithm
+// in the paper's order, so results are bit-identical to any correct
+// implementation of the same sequence.
+#pragma once
+#include <cstdint>
+
+namespace tf {
+
+struct d2 { double z0, z1; };
+
+// ------------------------------------------------------------------ bits
+__device__ __forceinline__ uint64_t bits_of(double v) { return (uint64_t)__double_as_longlong(v); }
+__device__ __forceinline__ double from_bits(uint64_t b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((bits_of(v) >> 52) & 0x7FF) != 0x7FF;
+}
+
+// ------------------------------------------------- Background: exact transforms
+
+// Algorithm 1.2 (Two-Sum): a + b -> s + t, t the exact rounding error.
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &t) {
+    s = __dadd_rn(a, b);
+    double bv = __dsub_rn(s, a);
+    double av = __dsub_rn(s, bv);
+    double br = __dsub_rn(b, bv);
+    double ar = __dsub_rn(a, av);
+    t = __dadd_rn(ar, br);
+}
+
+// Algorithm 2.2 (Two-Diff): a - b -> d + t.  Steps (4),(5) in Shewchuk's
+// order (b# = b' - b, a# = a - a'), which makes a - b = d + t exact.
+__device__ __forceinline__ void two_diff(double a, double b, double &d, double &t) {
+    d = __dsub_rn(a, b);
+    double bv = __dsub_rn(a, d);
+    double av = __dadd_rn(bv, d);
+    double br = __dsub_rn(bv, b);
+    double ar = __dsub_rn(a, av);
+    t = __dadd_rn(ar, br);
+}
+
+// Algorithm 3 (Two-Product-FMA): p = a*b, e = fma(a, b, -p).
+__device__ __forceinline__ void two_prod(double a, double b, double &p, double &e) {
+    p = __dmul_rn(a, b);
+    e = __fma_rn(a, b, -p);
+}
+
+// Algorithm 4: q = a/b, r = fma(-q, b, a) = a - q b exactly.
+__device__ __forceinline__ void div_rem(double a, double b, double &q, double &r) {
+    q = __ddiv_rn(a, b);
+    r = __fma_rn(-q, b, a);
+}
+
+// Algorithm 5: c = sqrt(a), d = fma(-c, c, a) = a - c^2 exactly.
+__device__ __forceinline__ void sqrt_rem(double a, double &c, double &d) {
+    c = __dsqrt_rn(a);
+    d = __fma_rn(-c, c, a);
+}
+
+// ----------------------------------------------------------- Algorithms
+
+// ATF1: z0 = x0 + y0; z1 = (x1 + y1) + err(x0 + y0).
+__device__ __forceinline__ d2 atf1(double x0, double x1, double y0, double y1) {
+    double s, e;
+    two_sum(x0, y0, s, e);
+    return {s, __dadd_rn(__dadd_rn(x1, y1), e)};
+}
+
+// ATF1.1: z0 = x0 + y0; z1 = x1 + err(x0 + y0).
+__device__ __forceinline__ d2 atf11(double x0, double x1, double y0) {
+    double s, e;
+    two_sum(x0, y0, s, e);
+    return {s, __dadd_rn(x1, e)};
+}
+
+// STF1: z0 = x0 - y0; z1 = (x1 - y1) + err(x0 - y0).
+__device__ __forceinline__ d2 stf1(double x0, double x1, double y0, double y1) {
+    double d, e;
+    two_diff(x0, y0, d, e);
+    return {d, __dadd_rn(__dsub_rn(x1, y1), e)};
+}
+
+// STF1.1: z0 = x0 - y0; z1 = x1 + err(x0 - y0).
+__device__ __forceinline__ d2 stf11(double x0, double x1, double y0) {
+    double d, e;
+    two_diff(x0, y0, d, e);
+    return {d, __dadd_rn(x1, e)};
+}
+
+// MTF1: z0 = p00; z1 = (e00 + p11) + (p01 + p10).
+__device__ __forceinline__ d2 mtf1(double x0, double x1, double y0, double y1) {
+    double p00, e00;
+    two_prod(x0, y0, p00, e00);
+    double p11 = __dmul_rn(x1, y1);
+    double p01 = __dmul_rn(x0, y1);
+    double p10 = __dmul_rn(x1, y0);
+    return {p00, __dadd_rn(__dadd_rn(e00, p11), __dadd_rn(p01, p10))};
+}
+
+// MTF1.1: z0 = p00; z1 = e00 + p10.
+__device__ __forceinline__ d2 mtf11(double x0, double x1, double y0) {
+    double p00, e00;
+    two_prod(x0, y0, p00, e00);
+    return {p00, __dadd_rn(e00, __dmul_rn(x1, y0))};
+}
+
+// DTF1.1.1: z0 = x0/y0; r1 = fma(-z0, y0, x0); z1 = r1/y0.
+__device__ __forceinline__ d2 dtf111(double x0, double y0) {
+    double q, r;
+    div_rem(x0, y0, q, r);
+    return {q, __ddiv_rn(r, y0)};
+}
+
+// DTF1.1: z0 = x0/y0; r = fma(-z0, y0, x0); c = r + x1; z1 = c/y0.
+__device__ __forceinline__ d2 dtf11(double x0, double x1, double y0) {
+    double q, r;
+    div_rem(x0, y0, q, r);
+    return {q, __ddiv_rn(__dadd_rn(r, x1), y0)};
+}
+
+// DTF1: z0 = x0/y0; r0 = fma(-z0, y0, x0); r1 = fma(-z0, y1, x1);
+//       c0 = r0 + r1; d0 = y0 + y1; z1 = c0/d0.
+__device__ __forceinline__ d2 dtf1(double x0, double x1, double y0, double y1) {
+    double q, r0;
+    div_rem(x0, y0, q, r0);
+    double r1 = __fma_rn(-q, y1, x1);
+    double c0 = __dadd_rn(r0, r1);
+    double d0 = __dadd_rn(y0, y1);
+    return {q, __ddiv_rn(c0, d0)};
+}
+
+// RPF1: z0 = sqrt(x0); z1 = (x1 + fma(-z0, z0, x0)) / (2 z0).
+__device__ __forceinline__ d2 rpf1(double x0, double x1) {
+    double c, d;
+    sqrt_rem(x0, c, d);
+    return {c, __ddiv_rn(__dadd_rn(x1, d), __dmul_rn(2.0, c))};
+}
+
+// RPF1.1: z0 = sqrt(x0); z1 = fma(-z0, z0, x0) / (2 z0).
+__device__ __forceinline__ d2 rpf11(double x0) {
+    double c, d;
+    sqrt_rem(x0, c, d);
+    return {c, __ddiv_rn(d, __dmul_rn(2.0, c))};
+}
+
+// RTF1: z0 = sqrt(x0); (u0,u1) = Two-Sum(x0, x1); (v0,v1) = RPF1(u0,u1);
+//       (w0,w1) = STF1.1((v0,v1), z0); z1 = w0 + w1.
+__device__ __forceinline__ d2 rtf1(double x0, double x1) {
+    double z0 = __dsqrt_rn(x0);
+    double u0, u1;
+    two_sum(x0, x1, u0, u1);
+    d2 v = rpf1(u0, u1);
+    d2 w = stf11(v.z0, v.z1, z0);
+    return {z0, __dadd_rn(w.z0, w.z1)};
+}
+
+// ------------------------------------------------------- operand kinds
+// Operand kinds: (twofold, twofold) general; (twofold, dotted) ".1";
+// (dotted, twofold) general with x1 = +0; (dotted, dotted) exact transform
+// or DTF1.1.1; sqrt of dotted: RPF1.1.
+enum Op : int { OP_ADD = 1, OP_SUB = 2, OP_MUL = 3, OP_DIV = 4, OP_SQRT = 5 };
+
+__device__ __forceinline__ d2 apply(int op, double x0, double x1, bool xd, double y0, double y1,
+                                    bool yd) {
+    if (op == OP_SQRT) return xd ? rpf11(x0) : rtf1(x0, x1);
+    if (xd && yd) {
+        d2 z;
+        switch (op) {
+        case OP_ADD: two_sum(x0, y0, z.z0, z.z1); return z;
+        case OP_SUB: two_diff(x0, y0, z.z0, z.z1); return z;
+        case OP_MUL: two_prod(x0, y0, z.z0, z.z1); return z;
+        default: return dtf111(x0, y0);
+        }
+    }
+    if (yd) {
+        switch (op) {
+        case OP_ADD: return atf11(x0, x1, y0);
+        case OP_SUB: return stf11(x0, x1, y0);
+        case OP_MUL: return mtf11(x0, x1, y0);
+        default: return dtf11(x0, x1, y0);
+        }
+    }
+    if (xd) x1 = 0.0;
+    switch (op) {
+    case OP_ADD: return atf1(x0, x1, y0, y1);
+    case OP_SUB: return stf1(x0, x1, y0, y1);
+    case OP_MUL: return mtf1(x0, x1, y0, y1);
+    default: return dtf1(x0, x1, y0, y1);
+    }
+}
+
+// Plain binary64 operation (the "dotted" arithmetic the twofold shadows).
+__device__ __forceinline__ double apply_plain(int op, double a, double b) {
+    switch (op) {
+    case OP_ADD: return __dadd_rn(a, b);
+    case OP_SUB: return __dsub_rn(a, b);
+    case OP_MUL: return __dmul_rn(a, b);
+    case OP_DIV: return __ddiv_rn(a, b);
+    default: return __dsqrt_rn(a);
+    }
+}
+
+// ---------------------------------------------------------- panic flag
+struct FlagCfg {
+    int mode;      // 0 REL, 1 ULP
+    double tau;    // REL threshold
+    double m;      // ULP threshold
+};
+
+// ulp(v) = 2^(max(e,-1022)-52) from the exponent field; NaN for Inf/NaN.
+__device__ __forceinline__ double ulp_of(double v) {
+    int e = (int)((bits_of(v) >> 52) & 0x7FF);
+    if (e == 0x7FF) return __longlong_as_double(0x7FF8000000000000LL);
+    if (e == 0) e = 1;
+    int p = e - 1075;                       // exponent of the ulp, >= -1074
+    if (p >= -1022) return from_bits((uint64_t)(p + 1023) << 52);
+    return from_bits(1ull << (p + 1074));   // subnormal power of two
+}
+
+__device__ __forceinline__ uint8_t flag_of(double z0, double z1, const FlagCfg &f) {
+    uint8_t r = 0;
+    if (!finite_bits(z0) || !finite_bits(z1)) r |= 2;
+    double lim = (f.mode == 0) ? __dmul_rn(f.tau, fabs(z0)) : __dmul_rn(f.m, ulp_of(z0));
+    if (fabs(z1) > lim) r |= 1;
+    return r;
+}
+
+}  // namespace tf

@@ -1,0 +1,172 @@
+// twofold_ew / plain_ew: straight-line programs of twofold operations over
+// arrays (the array functions vtadd2/vtadd1/vtadd... of the paper's C++
+// test code, generalised to a fused chain so intermediates never touch HBM).
+//
+// One thread evaluates one element at a time in a grid-stride loop.
+// Inputs are read from global memory when an instruction first needs them;
+// temporaries live in a per-thread column of shared memory (layout
+// [temp][hi|lo][thread], so a warp touches 32 consecutive words: no bank
+// conflicts).  The program is warp-uniform, so its dispatch never diverges.
+#include "tf_host.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+
+struct EwArgs {
+    int64_t n;
+    int nprog, nin, ntemp, last;
+    int8_t op[TF_EW_MAX_PROG], dst[TF_EW_MAX_PROG], a[TF_EW_MAX_PROG], b[TF_EW_MAX_PROG];
+    const double *hi[TF_EW_MAX_INPUTS];
+    const double *lo[TF_EW_MAX_INPUTS];
+    double *out_hi, *out_lo;
+    uint8_t *flags;
+    tf::FlagCfg fc;
+};
+
+__global__ void __launch_bounds__(kThreads) ew_kernel(const __grid_constant__ EwArgs A) {
+    extern __shared__ double regs[];   // [ntemp][2][kThreads]
+    const int t = threadIdx.x;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + t; i < A.n; i += (int64_t)gridDim.x * kThreads) {
+        for (int s = 0; s < A.nprog; ++s) {
+            const int op = A.op[s], ra = A.a[s], rb = A.b[s];
+            double x0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
+            bool xd = false, yd = true;
+            if (ra < A.nin) {
+                x0 = A.hi[ra][i];
+                xd = A.lo[ra] == nullptr;
+                if (!xd) x1 = A.lo[ra][i];
+            } else {
+                x0 = regs[((ra - A.nin) * 2 + 0) * kThreads + t];
+                x1 = regs[((ra - A.nin) * 2 + 1) * kThreads + t];
+            }
+            if (op != tf::OP_SQRT) {
+                if (rb < A.nin) {
+                    y0 = A.hi[rb][i];
+                    yd = A.lo[rb] == nullptr;
+                    if (!yd) y1 = A.lo[rb][i];
+                } else {
+                    y0 = regs[((rb - A.nin) * 2 + 0) * kThreads + t];
+                    y1 = regs[((rb - A.nin) * 2 + 1) * kThreads + t];
+                    yd = false;
+                }
+            }
+            tf::d2 z = tf::apply(op, x0, x1, xd, y0, y1, yd);
+            const int rd = A.dst[s] - A.nin;
+            regs[(rd * 2 + 0) * kThreads + t] = z.z0;
+            regs[(rd * 2 + 1) * kThreads + t] = z.z1;
+        }
+        const int rl = A.last - A.nin;
+        const double z0 = regs[(rl * 2 + 0) * kThreads + t];
+        const double z1 = regs[(rl * 2 + 1) * kThreads + t];
+        A.out_hi[i] = z0;
+        A.out_lo[i] = z1;
+        if (A.flags) A.flags[i] = tf::flag_of(z0, z1, A.fc);
+    }
+}
+
+struct PlainArgs {
+    int64_t n;
+    int nprog, nin, ntemp, last;
+    int8_t op[TF_EW_MAX_PROG], dst[TF_EW_MAX_PROG], a[TF_EW_MAX_PROG], b[TF_EW_MAX_PROG];
+    const double *in[TF_EW_MAX_INPUTS];
+    double *out;
+};
+
+__global__ void __launch_bounds__(kThreads) plain_ew_kernel(const __grid_constant__ PlainArgs A) {
+    extern __shared__ double regs[];   // [ntemp][kThreads]
+    const int t = threadIdx.x;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + t; i < A.n; i += (int64_t)gridDim.x * kThreads) {
+        for (int s = 0; s < A.nprog; ++s) {
+            const int op = A.op[s], ra = A.a[s], rb = A.b[s];
+            const double x = ra < A.nin ? A.in[ra][i] : regs[(ra - A.nin) * kThreads + t];
+            double y = 0.0;
+            if (op != tf::OP_SQRT) y = rb < A.nin ? A.in[rb][i] : regs[(rb - A.nin) * kThreads + t];
+            regs[(A.dst[s] - A.nin) * kThreads + t] = tf::apply_plain(op, x, y);
+        }
+        A.out[i] = regs[(A.last - A.nin) * kThreads + t];
+    }
+}
+
+// Validate a program; returns the number of temporaries needed or -1.
+int check_prog(const int32_t *prog, int nprog, int nin, int8_t *op, int8_t *dst, int8_t *a,
+               int8_t *b, int *last) {
+    if (!prog || nprog < 1 || nprog > TF_EW_MAX_PROG || nin < 1 || nin > TF_EW_MAX_INPUTS) return -1;
+    bool defined[TF_EW_MAX_REGS] = {};
+    for (int k = 0; k < nin; ++k) defined[k] = true;
+    int maxreg = nin - 1;
+    for (int s = 0; s < nprog; ++s) {
+        const int32_t o = prog[4 * s], d = prog[4 * s + 1], ra = prog[4 * s + 2];
+        int32_t rb = prog[4 * s + 3];
+        if (o < TF_ADD || o > TF_SQRT) return -1;
+        if (d < nin || d >= TF_EW_MAX_REGS) return -1;
+        if (ra < 0 || ra >= TF_EW_MAX_REGS || !defined[ra]) return -1;
+        if (o == TF_SQRT) rb = ra;
+        if (rb < 0 || rb >= TF_EW_MAX_REGS || !defined[rb]) return -1;
+        defined[d] = true;
+        if (d > maxreg) maxreg = d;
+        op[s] = (int8_t)o; dst[s] = (int8_t)d; a[s] = (int8_t)ra; b[s] = (int8_t)rb;
+        *last = d;
+    }
+    return maxreg + 1 - nin;
+}
+
+int grid_for(int64_t n, size_t smem, const void *kernel) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int64_t want = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)tfh::sm_count() * per_sm;
+    return (int)(want < cap ? want : cap);
+}
+
+}  // namespace
+
+extern "C" int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, int32_t nin,
+                          int64_t n, tf_out out, const tf_params *p, void *stream) {
+    EwArgs A{};
+    if (n < 0 || !in || !tfh::params_ok(p)) return TF_EINVAL;
+    A.ntemp = check_prog(prog, nprog, nin, A.op, A.dst, A.a, A.b, &A.last);
+    if (A.ntemp < 1) return TF_EINVAL;
+    if (!tfh::dptr_ok(out.hi) || !tfh::dptr_ok(out.lo)) return TF_EINVAL;
+    for (int k = 0; k < nin; ++k) {
+        if (!tfh::dptr_ok(in[k].hi) || !tfh::optr_ok(in[k].lo)) return TF_EINVAL;
+        A.hi[k] = in[k].hi;
+        A.lo[k] = in[k].lo;
+    }
+    if (n == 0) return TF_OK;
+    A.n = n; A.nprog = nprog; A.nin = nin;
+    A.out_hi = out.hi; A.out_lo = out.lo; A.flags = out.flags;
+    A.fc = tfh::flag_cfg(p);
+    const size_t smem = (size_t)A.ntemp * 2 * kThreads * sizeof(double);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(ew_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TF_ECUDA;
+    const int grid = grid_for(n, smem, (const void *)ew_kernel);
+    ew_kernel<<<grid, kThreads, smem, tfh::as_stream(stream)>>>(A);
+    return tfh::launch_status();
+}
+
+extern "C" int plain_ew(const int32_t *prog, int32_t nprog, const double *const *in, int32_t nin,
+                        int64_t n, double *out, void *stream) {
+    PlainArgs A{};
+    if (n < 0 || !in) return TF_EINVAL;
+    A.ntemp = check_prog(prog, nprog, nin, A.op, A.dst, A.a, A.b, &A.last);
+    if (A.ntemp < 1) return TF_EINVAL;
+    if (!tfh::dptr_ok(out)) return TF_EINVAL;
+    for (int k = 0; k < nin; ++k) {
+        if (!tfh::dptr_ok(in[k])) return TF_EINVAL;
+        A.in[k] = in[k];
+    }
+    if (n == 0) return TF_OK;
+    A.n = n; A.nprog = nprog; A.nin = nin; A.out = out;
+    const size_t smem = (size_t)A.ntemp * kThreads * sizeof(double);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(plain_ew_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return TF_ECUDA;
+    const int grid = grid_for(n, smem, (const void *)plain_ew_kernel);
+    plain_ew_kernel<<<grid, kThreads, smem, tfh::as_stream(stream)>>>(A);
+    return tfh::launch_status();
+}

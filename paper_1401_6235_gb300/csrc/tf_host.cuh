@@ -1,0 +1,56 @@
+// Host-side helpers shared by the library's translation units: parameter
+// defaults, argument checks, launch-error mapping.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/twofold.h"
+#include "tf_device.cuh"
+
+namespace tfh {
+
+constexpr double kDefaultTau = 0x1p-40;
+constexpr double kDefaultUlps = 4096.0;
+constexpr int kDefaultLeaf = 256;
+
+inline tf::FlagCfg flag_cfg(const tf_params *p) {
+    tf::FlagCfg f;
+    f.mode = p ? p->panic_mode : TF_PANIC_REL;
+    f.tau = p ? p->panic_tau : kDefaultTau;
+    f.m = p ? p->panic_ulps : kDefaultUlps;
+    return f;
+}
+
+inline bool params_ok(const tf_params *p) {
+    if (!p) return true;
+    if (p->panic_mode != TF_PANIC_REL && p->panic_mode != TF_PANIC_ULP) return false;
+    if (p->leaf < 1) return false;
+    return true;
+}
+
+inline int leaf_of(const tf_params *p) { return p ? p->leaf : kDefaultLeaf; }
+
+inline bool aligned8(const void *ptr) { return ((uintptr_t)ptr & 7u) == 0; }
+inline bool dptr_ok(const void *ptr) { return ptr != nullptr && aligned8(ptr); }
+inline bool optr_ok(const void *ptr) { return ptr == nullptr || aligned8(ptr); }
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int launch_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TF_OK : TF_ECUDA;
+}
+
+inline int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 148;
+    }
+    return sms;
+}
+
+}  // namespace tfh

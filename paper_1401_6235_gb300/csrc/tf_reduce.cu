@@ -1,0 +1,305 @@
+// Twofold sum and dot (and their plain binary64 twins) in the fixed
+// blocked-pairwise order, single or batched.
+//
+// Order (also in twofold.h): leaves of L consecutive elements, each
+// accumulated left to right into a twofold from (+0, +0) with ATF1 (the
+// paper's twofold accumulator, "2x" section: adding a plain value is strict
+// per step); leaf results combined by a bottom-up pairwise ATF1 tree with
+// an odd last node carried up.  Node i of level j covers leaves
+// [i 2^j, min((i+1) 2^j, m)), so an aligned block of B = 2^k leaves is a
+// subtree: reduce_blocks handles one block per CTA (one leaf per thread,
+// then an in-place strided tree in shared memory) and reduce_final
+// combines the partials of each job with the same tree.  Results therefore
+// do not depend on B, the grid or the device.
+#include <vector>
+
+#include "tf_host.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;        // = maximum leaves per block
+constexpr int kInlineJobs = 32;      // job tables up to this size travel in the launch params
+
+struct Tab {
+    const int64_t *offs;   // device job table (njobs+1), or nullptr: use the inline copy
+    const int64_t *blk0;
+    int64_t ioffs[kInlineJobs + 1];
+    int64_t iblk0[kInlineJobs + 1];
+    __device__ __forceinline__ int64_t off(int j) const { return offs ? offs[j] : ioffs[j]; }
+    __device__ __forceinline__ int64_t b0(int j) const { return blk0 ? blk0[j] : iblk0[j]; }
+};
+
+struct RedArgs {
+    const double *xh, *xl, *yh, *yl;
+    int njobs;
+    int64_t L;
+    int B;                     // leaves per block (power of two, <= kThreads)
+    Tab tab;
+    double *part0, *part1;     // partial results, one per block
+    double *out_hi, *out_lo;
+    uint8_t *flags;
+    tf::FlagCfg fc;
+};
+
+// Job of block b: the largest j with blk0[j] <= b (empty jobs own no block).
+__device__ __forceinline__ int job_of(const Tab &T, int njobs, int64_t b) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (T.b0(mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool DOT, bool PLAIN>
+__device__ __forceinline__ tf::d2 leaf(const RedArgs &A, int64_t b, int64_t e) {
+    tf::d2 acc = {0.0, 0.0};
+    const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
+    for (int64_t i = b; i < e; ++i) {
+        if (PLAIN) {
+            double term = DOT ? __dmul_rn(A.xh[i], A.yh[i]) : A.xh[i];
+            acc.z0 = __dadd_rn(acc.z0, term);
+        } else if (!DOT) {
+            acc = xd ? tf::atf11(acc.z0, acc.z1, A.xh[i]) : tf::atf1(acc.z0, acc.z1, A.xh[i], A.xl[i]);
+        } else {
+            tf::d2 p = tf::apply(tf::OP_MUL, A.xh[i], xd ? 0.0 : A.xl[i], xd, A.yh[i],
+                                 yd ? 0.0 : A.yl[i], yd);
+            acc = tf::atf1(acc.z0, acc.z1, p.z0, p.z1);
+        }
+    }
+    return acc;
+}
+
+template <bool PLAIN>
+__device__ __forceinline__ tf::d2 combine(tf::d2 l, tf::d2 r) {
+    if (PLAIN) return {__dadd_rn(l.z0, r.z0), 0.0};
+    return tf::atf1(l.z0, l.z1, r.z0, r.z1);
+}
+
+template <bool PLAIN>
+__device__ __forceinline__ void write_result(const RedArgs &A, int j, tf::d2 r) {
+    A.out_hi[j] = r.z0;
+    if (!PLAIN) {
+        A.out_lo[j] = r.z1;
+        if (A.flags) A.flags[j] = tf::flag_of(r.z0, r.z1, A.fc);
+    }
+}
+
+template <bool DOT, bool PLAIN>
+__global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant__ RedArgs A) {
+    __shared__ double s0[kThreads], s1[kThreads];
+    const int t = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    const int j = job_of(A.tab, A.njobs, b);
+    const int64_t e0 = A.tab.off(j), len = A.tab.off(j + 1) - e0;
+    const int64_t m = (len + A.L - 1) / A.L;
+    const int64_t leaf0 = (b - A.tab.b0(j)) * A.B;
+    const int nl = (int)min((int64_t)A.B, m - leaf0);
+    if (t < nl) {
+        const int64_t lb = e0 + (leaf0 + t) * A.L;
+        const int64_t le = min(lb + A.L, e0 + len);
+        tf::d2 r = leaf<DOT, PLAIN>(A, lb, le);
+        s0[t] = r.z0;
+        s1[t] = r.z1;
+    }
+    __syncthreads();
+    for (int s = 1; s < nl; s <<= 1) {
+        if ((t & (2 * s - 1)) == 0 && t + s < nl) {
+            tf::d2 r = combine<PLAIN>({s0[t], s1[t]}, {s0[t + s], s1[t + s]});
+            s0[t] = r.z0;
+            s1[t] = r.z1;
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const tf::d2 r = {s0[0], s1[0]};
+        if (A.tab.b0(j + 1) - A.tab.b0(j) == 1) write_result<PLAIN>(A, j, r);
+        else { A.part0[b] = r.z0; A.part1[b] = r.z1; }
+    }
+}
+
+// One CTA per job with 0 or >= 2 blocks.  Thread t first reduces the aligned
+// group of G partials [tG, (t+1)G) in place (G = 2^g, G*kThreads >= nb),
+// which is a subtree, then the CTA reduces the group roots.
+template <bool PLAIN>
+__global__ void __launch_bounds__(kThreads) reduce_final(const __grid_constant__ RedArgs A) {
+    __shared__ double s0[kThreads], s1[kThreads];
+    const int j = blockIdx.x, t = threadIdx.x;
+    const int64_t p0 = A.tab.b0(j), nb = A.tab.b0(j + 1) - p0;
+    if (nb == 1) return;
+    if (nb == 0) {
+        if (t == 0) write_result<PLAIN>(A, j, {0.0, 0.0});
+        return;
+    }
+    int64_t G = 1;
+    while (G * kThreads < nb) G <<= 1;
+    const int ng = (int)((nb + G - 1) / G);
+    if (t < ng) {
+        double *q0 = A.part0 + p0 + (int64_t)t * G, *q1 = A.part1 + p0 + (int64_t)t * G;
+        const int64_t cnt = min(G, nb - (int64_t)t * G);
+        for (int64_t s = 1; s < cnt; s <<= 1)
+            for (int64_t i = 0; i + s < cnt; i += 2 * s) {
+                tf::d2 r = combine<PLAIN>({q0[i], q1[i]}, {q0[i + s], q1[i + s]});
+                q0[i] = r.z0;
+                q1[i] = r.z1;
+            }
+        s0[t] = q0[0];
+        s1[t] = q1[0];
+    }
+    __syncthreads();
+    for (int s = 1; s < ng; s <<= 1) {
+        if ((t & (2 * s - 1)) == 0 && t + s < ng) {
+            tf::d2 r = combine<PLAIN>({s0[t], s1[t]}, {s0[t + s], s1[t + s]});
+            s0[t] = r.z0;
+            s1[t] = r.z1;
+        }
+        __syncthreads();
+    }
+    if (t == 0) write_result<PLAIN>(A, j, {s0[0], s1[0]});
+}
+
+// Leaves per block: at least ~1024 blocks while that keeps blocks >= 1 leaf.
+int leaves_per_block(int64_t M) {
+    int B = 1;
+    while (B < kThreads && (int64_t)B * 2 * 1024 <= M) B <<= 1;
+    return B;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Workspace: [offs (njobs+1) | blk0 (njobs+1)] [part0 (nblk)] [part1 (nblk)].
+size_t ws_need(int njobs, int64_t nblk) {
+    return align256(sizeof(int64_t) * 2 * (size_t)(njobs + 1)) + 2 * align256(sizeof(double) * (size_t)nblk);
+}
+
+template <bool DOT, bool PLAIN>
+int run(const double *xh, const double *xl, const double *yh, const double *yl, const int64_t *offs,
+        int njobs, double *out_hi, double *out_lo, uint8_t *flags, const tf_params *p, void *ws,
+        size_t ws_bytes, void *stream) {
+    if (njobs < 0 || !offs || !tfh::params_ok(p)) return TF_EINVAL;
+    if (njobs == 0) return TF_OK;
+    if (!tfh::dptr_ok(out_hi) || (!PLAIN && !tfh::dptr_ok(out_lo))) return TF_EINVAL;
+    if (offs[0] < 0) return TF_EINVAL;
+    for (int j = 0; j < njobs; ++j)
+        if (offs[j + 1] < offs[j]) return TF_EINVAL;
+    const int64_t ntot = offs[njobs];
+    if (ntot > 0) {
+        if (!tfh::dptr_ok(xh) || !tfh::optr_ok(xl)) return TF_EINVAL;
+        if (DOT && (!tfh::dptr_ok(yh) || !tfh::optr_ok(yl))) return TF_EINVAL;
+    }
+    const int64_t L = tfh::leaf_of(p);
+    std::vector<int64_t> tab(2 * (size_t)(njobs + 1));
+    int64_t M = 0;
+    for (int j = 0; j < njobs; ++j) M += (offs[j + 1] - offs[j] + L - 1) / L;
+    const int B = leaves_per_block(M);
+    int64_t nblk = 0;
+    bool need_final = false;
+    for (int j = 0; j < njobs; ++j) {
+        tab[j] = offs[j];
+        tab[njobs + 1 + j] = nblk;
+        const int64_t m = (offs[j + 1] - offs[j] + L - 1) / L;
+        const int64_t nb = (m + B - 1) / B;
+        need_final |= (nb != 1);
+        nblk += nb;
+    }
+    tab[njobs] = offs[njobs];
+    tab[2 * (size_t)njobs + 1] = nblk;
+    if (nblk > 0x7FFFFFFFLL) return TF_EUNSUPPORTED;
+
+    RedArgs A{};
+    A.xh = xh; A.xl = xl; A.yh = yh; A.yl = yl;
+    A.njobs = njobs; A.L = L; A.B = B;
+    A.out_hi = out_hi; A.out_lo = out_lo; A.flags = PLAIN ? nullptr : flags;
+    A.fc = tfh::flag_cfg(p);
+    cudaStream_t s = tfh::as_stream(stream);
+    const bool inl = njobs <= kInlineJobs;
+    size_t need = 0;
+    if (!inl) need += align256(sizeof(int64_t) * tab.size());
+    if (need_final && nblk > 0) need += 2 * align256(sizeof(double) * (size_t)nblk);
+    if (need > 0 && (!ws || ws_bytes < need || !tfh::aligned8(ws))) return TF_ENOSPC;
+    char *w = static_cast<char *>(ws);
+    if (inl) {
+        for (int j = 0; j <= njobs; ++j) {
+            A.tab.ioffs[j] = tab[j];
+            A.tab.iblk0[j] = tab[njobs + 1 + j];
+        }
+    } else {
+        A.tab.offs = reinterpret_cast<int64_t *>(w);
+        A.tab.blk0 = A.tab.offs + (njobs + 1);
+        if (cudaMemcpyAsync(w, tab.data(), tab.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return TF_ECUDA;
+        w += align256(sizeof(int64_t) * tab.size());
+    }
+    if (need_final && nblk > 0) {
+        A.part0 = reinterpret_cast<double *>(w);
+        A.part1 = reinterpret_cast<double *>(w + align256(sizeof(double) * (size_t)nblk));
+    }
+    if (nblk > 0) reduce_blocks<DOT, PLAIN><<<(unsigned)nblk, kThreads, 0, s>>>(A);
+    if (need_final) reduce_final<PLAIN><<<njobs, kThreads, 0, s>>>(A);
+    return tfh::launch_status();
+}
+
+}  // namespace
+
+extern "C" size_t twofold_workspace_bytes(int32_t kind, int64_t n_total, int32_t njobs,
+                                          const tf_params *p) {
+    (void)kind;
+    if (n_total < 0 || njobs < 1) return 0;
+    const int64_t L = p && p->leaf >= 1 ? p->leaf : tfh::kDefaultLeaf;
+    const int64_t Mmax = n_total / L + njobs;            // >= sum of ceil(len_j / L)
+    // blocks <= M/B + njobs with B = leaves_per_block(M): M/B < 2048 or B = 256
+    int64_t per = Mmax / kThreads + 1;
+    if (per < 2048) per = 2048;
+    const int64_t nblk = per + njobs;
+    return ws_need(njobs, nblk);
+}
+
+extern "C" int twofold_sum(tf_in x, int64_t n, tf_out out1, const tf_params *p, void *ws,
+                           size_t ws_bytes, void *stream) {
+    if (n < 0) return TF_EINVAL;
+    const int64_t offs[2] = {0, n};
+    return run<false, false>(x.hi, x.lo, nullptr, nullptr, offs, 1, out1.hi, out1.lo, out1.flags, p, ws,
+                             ws_bytes, stream);
+}
+
+extern "C" int twofold_dot(tf_in x, tf_in y, int64_t n, tf_out out1, const tf_params *p, void *ws,
+                           size_t ws_bytes, void *stream) {
+    if (n < 0) return TF_EINVAL;
+    const int64_t offs[2] = {0, n};
+    return run<true, false>(x.hi, x.lo, y.hi, y.lo, offs, 1, out1.hi, out1.lo, out1.flags, p, ws, ws_bytes,
+                            stream);
+}
+
+extern "C" int twofold_sum_batched(tf_in x, const int64_t *offs, int32_t njobs, tf_out out,
+                                   const tf_params *p, void *ws, size_t ws_bytes, void *stream) {
+    return run<false, false>(x.hi, x.lo, nullptr, nullptr, offs, njobs, out.hi, out.lo, out.flags, p, ws,
+                             ws_bytes, stream);
+}
+
+extern "C" int twofold_dot_batched(tf_in x, tf_in y, const int64_t *offs, int32_t njobs, tf_out out,
+                                   const tf_params *p, void *ws, size_t ws_bytes, void *stream) {
+    return run<true, false>(x.hi, x.lo, y.hi, y.lo, offs, njobs, out.hi, out.lo, out.flags, p, ws,
+                            ws_bytes, stream);
+}
+
+extern "C" int plain_sum(const double *x, int64_t n, double *out1, const tf_params *p, void *ws,
+                         size_t ws_bytes, void *stream) {
+    if (n < 0) return TF_EINVAL;
+    const int64_t offs[2] = {0, n};
+    return run<false, true>(x, nullptr, nullptr, nullptr, offs, 1, out1, nullptr, nullptr, p, ws, ws_bytes,
+                            stream);
+}
+
+extern "C" int plain_dot(const double *x, const double *y, int64_t n, double *out1, const tf_params *p,
+                         void *ws, size_t ws_bytes, void *stream) {
+    if (n < 0) return TF_EINVAL;
+    const int64_t offs[2] = {0, n};
+    return run<true, true>(x, nullptr, y, nullptr, offs, 1, out1, nullptr, nullptr, p, ws, ws_bytes, stream);
+}
+
+extern "C" int plain_dot_batched(const double *x, const double *y, const int64_t *offs, int32_t njobs,
+                                 double *out, const tf_params *p, void *ws, size_t ws_bytes, void *stream) {
+    return run<true, true>(x, nullptr, y, nullptr, offs, njobs, out, nullptr, nullptr, p, ws, ws_bytes,
+                           stream);
+}

@@ -1,0 +1,114 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol
+that include/twofold.h declares, and rejects bad arguments on the host
+before any launch (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__ as entry
+import paper_1401_6235_gb300 as T
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "twofold.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    entry.build()
+    return T.lib()
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_]+)\s*\(", src)) - {"sizeof"})
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 17
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in T.SIGNATURES, f"binding lacks {name}"
+
+
+def test_binding_names_match_header():
+    assert sorted(T.SIGNATURES) == declared()
+
+
+def test_strerror_and_version(L):
+    assert T.strerror(0) == "ok"
+    assert T.strerror(-2) == "workspace too small"
+    assert L.twofold_version() >= 100
+
+
+def _prog(rows):
+    return np.ascontiguousarray(np.asarray(rows, np.int32).reshape(-1, 4))
+
+
+FAKE = 1 << 20       # an aligned non-null address: never dereferenced by the host checks
+
+
+def _call_ew(L, rows, nin=2, n=10, out_hi=FAKE, in_lo=None):
+    p = _prog(rows)
+    ins = (T.tf_in * nin)(*[T.tf_in(FAKE, in_lo) for _ in range(nin)])
+    out = T.tf_out(out_hi, FAKE, None)
+    return L.twofold_ew(p.ctypes.data, p.shape[0], ins, nin, n, out, None, None)
+
+
+@pytest.mark.parametrize("rows", [
+    [(9, 2, 0, 1)],                 # unknown op
+    [(1, 1, 0, 1)],                 # writes an input register
+    [(1, 2, 0, 3)],                 # reads an undefined register
+    [(1, 40, 0, 1)],                # register out of range
+    [(1, 2, 5, 1)],                 # reads an undefined register
+    [(1, 3, 2, 0), (1, 2, 0, 1)],   # reads a temporary before it is written
+])
+def test_ew_rejects_bad_programs(L, rows):
+    assert _call_ew(L, rows) == T.TF_EINVAL
+
+
+def test_ew_rejects_bad_pointers_and_sizes(L):
+    ok = [(1, 2, 0, 1)]
+    assert _call_ew(L, ok, n=-1) == T.TF_EINVAL
+    assert _call_ew(L, ok, out_hi=None) == T.TF_EINVAL
+    assert _call_ew(L, ok, out_hi=FAKE + 4) == T.TF_EINVAL          # misaligned
+    assert _call_ew(L, ok, in_lo=FAKE + 2) == T.TF_EINVAL
+    assert _call_ew(L, ok, n=0) == T.TF_OK                           # nothing to do, no launch
+    too_long = [(1, 2, 0, 1)] * 33
+    assert _call_ew(L, too_long) == T.TF_EINVAL
+
+
+def test_reduce_rejects_bad_offsets_and_small_workspace(L):
+    x = T.tf_in(FAKE, None)
+    out = T.tf_out(FAKE, FAKE, None)
+    offs = np.array([0, 10, 5], np.int64)
+    assert L.twofold_dot_batched(x, x, offs.ctypes.data, 2, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    offs = np.array([-1, 5], np.int64)
+    assert L.twofold_sum_batched(x, offs.ctypes.data, 1, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    # 40 jobs (job table in the workspace) with a 16-byte workspace
+    offs = np.arange(41, dtype=np.int64) * 100
+    assert L.twofold_dot_batched(x, x, offs.ctypes.data, 40, out, None, FAKE, 16, None) == T.TF_ENOSPC
+    bad = T.params(leaf=0)
+    assert L.twofold_dot(x, x, 100, out, ctypes.byref(bad), FAKE, 1 << 20, None) == T.TF_EINVAL
+    bad = T.params(panic_mode=7)
+    assert L.twofold_sum(x, 100, out, ctypes.byref(bad), FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_sum(x, -5, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+
+
+def test_workspace_bound_covers_every_split(L):
+    """The workspace query is an upper bound of what the call needs for any
+    job mix with that total length (host arithmetic only)."""
+    for n, nj in [(0, 1), (1, 1), (65536, 1), (1 << 28, 4096), (1000, 1000), (1 << 20, 3)]:
+        b = L.twofold_workspace_bytes(T.KIND_DOT, n, nj, None)
+        assert b >= 16 * (nj + 1) + 2 * 8 * 2048
+
+
+def test_horner_rejects_bad_degree(L):
+    out = T.tf_out(FAKE, FAKE, None)
+    assert L.twofold_horner(FAKE, -1, FAKE, 10, out, None, None) == T.TF_EINVAL
+    assert L.twofold_horner(FAKE, 5000, FAKE, 10, out, None, None) == T.TF_EINVAL
+    assert L.twofold_horner(FAKE, 3, FAKE, 0, out, None, None) == T.TF_OK

@@ -1,0 +1,157 @@
+"""GPU parity of twofold_ew / plain_ew (through the C ABI) with the oracle:
+bit-exact z0, z1 and flags on every op and operand kind, on edge values, on
+random programs, on the elementwise chain z = sqrt((a*b + c)/d) at several
+tile-spanning sizes with ragged tails, and at the full 2^28 size on sampled
+outputs."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1401_6235_gb300 as T
+import synth
+from tests.fp import rand_doubles, rand_tails
+from tests.gpu_util import SPECIAL, assert_bits, assert_flags, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as e
+    e.build()
+
+
+def edge_operands():
+    """All pairs of special heads, each with a few tails."""
+    tails = np.array([0.0, -0.0, 1e-17, -3e-300, 2.0 ** -1074, np.inf, np.nan, 0.25])
+    rng = np.random.default_rng(0)
+    x0, y0 = [a.ravel() for a in np.meshgrid(SPECIAL, SPECIAL)]
+    reps = 4
+    x0 = np.tile(x0, reps)
+    y0 = np.tile(y0, reps)
+    x1 = tails[rng.integers(0, tails.size, x0.size)]
+    y1 = tails[rng.integers(0, tails.size, y0.size)]
+    x1[: SPECIAL.size ** 2] = 0.0
+    y1[: SPECIAL.size ** 2] = 0.0
+    return x0, x1, y0, y1
+
+
+def random_operands(n=200003, seed=1):
+    rng = np.random.default_rng(seed)
+    x0 = rand_doubles(rng, n, -80, 80)
+    y0 = rand_doubles(rng, n, -80, 80)
+    return x0, rand_tails(rng, x0, 0, 70), y0, rand_tails(rng, y0, 0, 70)
+
+
+@pytest.mark.parametrize("op", [O.ADD, O.SUB, O.MUL, O.DIV, O.SQRT])
+@pytest.mark.parametrize("xd,yd", list(itertools.product([False, True], repeat=2)))
+@pytest.mark.parametrize("data", ["edge", "random"])
+def test_single_op_kinds(op, xd, yd, data):
+    x0, x1, y0, y1 = edge_operands() if data == "edge" else random_operands()
+    prog = [(op, 2, 0, 1)]
+    ins = [(x0, None if xd else x1), (y0, None if yd else y1)]
+    r0, r1, rf = O.ew(prog, ins)
+    g = [(dev(h), None if lo is None else dev(lo)) for h, lo in ins]
+    z0, z1, fl = T.twofold_ew(prog, g)
+    assert_bits(z0, r0, "z0")
+    assert_bits(z1, r1, "z1")
+    assert_flags(fl, rf, "flags")
+    pz = T.plain_ew(prog, [g[0][0], g[1][0]])
+    assert_bits(pz, O.ew_plain(prog, [x0, y0]), "plain")
+    assert_bits(pz, r0, "plain == z0")
+
+
+@pytest.mark.parametrize("n", [1, 31, 128, 129, 4097, 100003, (1 << 20) + 13])
+def test_chain_config_sizes(n):
+    d = synth.ew_chain(n, seed=n)
+    ins = [(d["a0"], d["a1"]), (d["b0"], d["b1"]), (d["c0"], d["c1"]), (d["d0"], d["d1"])]
+    r0, r1, rf = O.ew(T.CHAIN_SQRT_MAD_DIV, ins)
+    g = [(dev(h), dev(lo)) for h, lo in ins]
+    z0, z1, fl = T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, g)
+    assert_bits(z0, r0, "z0")
+    assert_bits(z1, r1, "z1")
+    assert_flags(fl, rf, "flags")
+    pz = T.plain_ew(T.CHAIN_SQRT_MAD_DIV, [h for h, _ in g])
+    assert_bits(pz, r0, "plain twin == z0")
+
+
+@pytest.mark.parametrize("mode", [T.PANIC_REL, T.PANIC_ULP])
+def test_chain_flag_modes(mode):
+    n = 50001
+    d = synth.ew_chain(n, seed=3)
+    ins = [(d["a0"], d["a1"]), (d["b0"], d["b1"]), (d["c0"], d["c1"]), (d["d0"], d["d1"])]
+    tau, m = 2.0 ** -52, 3.0
+    p = T.params(panic_mode=mode, panic_tau=tau, panic_ulps=m)
+    r0, r1, rf = O.ew(T.CHAIN_SQRT_MAD_DIV, ins, mode=mode, tau=tau, m=m)
+    z0, z1, fl = T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, [(dev(h), dev(lo)) for h, lo in ins], p=p)
+    assert_flags(fl, rf, "flags")
+    assert 0 < np.mean(rf & 1) < 1
+
+
+def test_random_programs():
+    rng = np.random.default_rng(11)
+    n = 30011
+    for trial in range(12):
+        nin = int(rng.integers(1, 6))
+        ins_np = []
+        for k in range(nin):
+            h = rand_doubles(rng, n, -6, 6)
+            if k % 2 == 0:
+                h = np.abs(h)
+            lo = None if rng.random() < 0.4 else rand_tails(rng, h, 20, 60)
+            ins_np.append((h, lo))
+        prog, defined = [], list(range(nin))
+        nsteps = int(rng.integers(1, 10))
+        for s in range(nsteps):
+            op = int(rng.integers(1, 6))
+            dst = nin + s
+            a, b = int(rng.choice(defined)), int(rng.choice(defined))
+            prog.append((op, dst, a, b if op != O.SQRT else a))
+            defined.append(dst)
+        r0, r1, rf = O.ew(prog, ins_np)
+        g = [(dev(h), None if lo is None else dev(lo)) for h, lo in ins_np]
+        z0, z1, fl = T.twofold_ew(prog, g)
+        assert_bits(z0, r0, f"trial {trial} z0")
+        assert_bits(z1, r1, f"trial {trial} z1")
+        assert_flags(fl, rf, f"trial {trial} flags")
+        assert_bits(T.plain_ew(prog, [h for h, _ in g]), r0, f"trial {trial} plain")
+
+
+def test_deterministic_and_empty():
+    d = synth.ew_chain(70001, seed=9)
+    g = [(dev(d[k + "0"]), dev(d[k + "1"])) for k in "abcd"]
+    a = [host(t) for t in T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, g)]
+    b = [host(t) for t in T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, g)]
+    for u, v in zip(a, b):
+        assert np.array_equal(u.view(np.uint8), v.view(np.uint8))
+    import torch
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    z0, z1, fl = T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, [(e, e)] * 4)
+    assert z0.numel() == 0
+
+
+def test_chain_full_size_sampled():
+    """The full workload (n = 2^28) in the launch configuration the benchmark
+    times, checked on 2^20 sampled elements against the oracle."""
+    import torch
+    n = 1 << 28
+    d = synth.ew_chain(n, seed=0)
+    g = {k: dev(v) for k, v in d.items()}
+    ins = [(g["a0"], g["a1"]), (g["b0"], g["b1"]), (g["c0"], g["c1"]), (g["d0"], g["d1"])]
+    z0, z1, fl = T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, ins)
+    pz = T.plain_ew(T.CHAIN_SQRT_MAD_DIV, [h for h, _ in ins])
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(0).choice(n, 1 << 20, replace=False))
+    idx[:4] = [0, 1, n - 2, n - 1]
+    idx = np.unique(idx)
+    sub = [(d[k + "0"][idx], d[k + "1"][idx]) for k in "abcd"]
+    r0, r1, rf = O.ew(T.CHAIN_SQRT_MAD_DIV, sub)
+    ti = torch.from_numpy(idx).to("cuda")
+    assert_bits(z0[ti], r0, "z0")
+    assert_bits(z1[ti], r1, "z1")
+    assert_flags(fl[ti], rf, "flags")
+    assert_bits(pz[ti], r0, "plain twin")
+    del g, ins, z0, z1, fl, pz
+    torch.cuda.empty_cache()

@@ -1,0 +1,136 @@
+"""GPU parity of the sum and dot entry points (C ABI) with the oracle: bit-
+exact z0, z1 and flags for every operand kind, leaf sizes, sizes that span
+several blocks with ragged tails, empty input, uneven and empty batched
+jobs, the n = 65536 dot and the 4096 x 2^16 ill-conditioned batch in full."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1401_6235_gb300 as T
+import synth
+from tests.fp import rand_tails
+from tests.gpu_util import assert_bits, assert_flags, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as e
+    e.build()
+
+
+def tails(x, seed):
+    return rand_tails(np.random.default_rng(seed), x, 30, 60)
+
+
+SIZES = [0, 1, 2, 255, 256, 257, 65536, 65537, 1000003]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("kinds", ["dd", "tt", "td", "dt"])
+def test_dot_kinds_sizes(n, kinds):
+    x, y = synth.dot_uniform(n, seed=n + 1)
+    xl = tails(x, 1) if kinds[0] == "t" else None
+    yl = tails(y, 2) if kinds[1] == "t" else None
+    e0, e1 = O.reduce(x, xl, y, yl, L=256)
+    z0, z1, fl = T.twofold_dot(dev(x), dev(y), None if xl is None else dev(xl),
+                               None if yl is None else dev(yl))
+    assert_bits(z0, [e0], "z0")
+    assert_bits(z1, [e1], "z1")
+    assert_flags(fl, [O.flag(e0, e1)], "flag")
+    if kinds == "dd":
+        assert_bits(T.plain_dot(dev(x), dev(y)), [O.reduce_plain(x, y)], "plain")
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("dotted", [True, False])
+def test_sum_sizes(n, dotted):
+    x, _ = synth.dot_uniform(n, seed=n + 7)
+    xl = None if dotted else tails(x, 3)
+    e0, e1 = O.reduce(x, xl, L=256)
+    z0, z1, fl = T.twofold_sum(dev(x), None if xl is None else dev(xl))
+    assert_bits(z0, [e0], "z0")
+    assert_bits(z1, [e1], "z1")
+    assert_flags(fl, [O.flag(e0, e1)], "flag")
+    if dotted:
+        assert_bits(T.plain_sum(dev(x)), [O.reduce_plain(x)], "plain")
+
+
+@pytest.mark.parametrize("L", [1, 3, 7, 64, 1000, 1 << 20])
+def test_leaf_sizes(L):
+    n = 300007
+    x, y = synth.dot_uniform(n, seed=L)
+    p = T.params(leaf=L)
+    e0, e1 = O.reduce(x, None, y, None, L=L)
+    z0, z1, fl = T.twofold_dot(dev(x), dev(y), p=p)
+    assert_bits(z0, [e0], f"L={L} z0")
+    assert_bits(z1, [e1], f"L={L} z1")
+    assert_bits(T.plain_dot(dev(x), dev(y), p=p), [O.reduce_plain(x, y, L=L)], "plain")
+
+
+def test_config_dot_65536_zero_tails_equal_dotted():
+    """n = 65536 uniform[-1,1] seed 0: tails materialised as +0 and tails
+    absent give the same bits, equal to the oracle."""
+    import torch
+    x, y = synth.dot_uniform(65536, seed=0)
+    e0, e1 = O.reduce(x, None, y, None)
+    a = T.twofold_dot(dev(x), dev(y))
+    z = torch.zeros(65536, dtype=torch.float64, device="cuda")
+    b = T.twofold_dot(dev(x), dev(y), z, z)
+    for t in (a, b):
+        assert_bits(t[0], [e0], "z0")
+        assert_bits(t[1], [e1], "z1")
+        assert_flags(t[2], [O.flag(e0, e1)], "flag")
+
+
+def test_batched_uneven_with_empty_jobs():
+    rng = np.random.default_rng(5)
+    lens = rng.integers(0, 200000, 70)
+    lens[[0, 5, 6, 69]] = 0
+    lens[10] = 1
+    lens[11] = 256
+    lens[12] = 1 << 20
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    n = int(offs[-1])
+    x, y = synth.dot_uniform(n, seed=77)
+    xl = tails(x, 9)
+    r0, r1, rf = O.dot_batched(x, xl, y, None, offs)
+    z0, z1, fl = T.twofold_dot_batched(dev(x), dev(y), offs, xl=dev(xl))
+    assert_bits(z0, r0, "z0")
+    assert_bits(z1, r1, "z1")
+    assert_flags(fl, rf, "flags")
+    s0, s1, sf = O.sum_batched(x, xl, offs)
+    q0, q1, qf = T.twofold_sum_batched(dev(x), offs, xl=dev(xl))
+    assert_bits(q0, s0, "sum z0")
+    assert_bits(q1, s1, "sum z1")
+    assert_flags(qf, sf, "sum flags")
+    pl = np.array([O.reduce_plain(x[a:b], y[a:b]) for a, b in zip(offs[:-1], offs[1:])])
+    assert_bits(T.plain_dot_batched(dev(x), dev(y), offs), pl, "plain batched")
+
+
+def test_batched_offset_start_and_few_jobs():
+    """Jobs need not start at 0 and small tables travel in the launch."""
+    x, y = synth.dot_uniform(100000, seed=4)
+    offs = np.array([1000, 1000, 1257, 99999], np.int64)
+    r0, r1, rf = O.dot_batched(x, None, y, None, offs)
+    z0, z1, fl = T.twofold_dot_batched(dev(x), dev(y), offs)
+    assert_bits(z0, r0, "z0")
+    assert_bits(z1, r1, "z1")
+
+
+def test_ill_conditioned_batch_full():
+    """4096 dots of 2^16 with condition 10^U(2,30): bit-exact in full; the
+    panic rate grows with the realised condition number."""
+    x, y, offs, exact, cond, _ = synth.cond_dots(4096, 1 << 16, seed=0)
+    r0, r1, rf = O.dot_batched(x, None, y, None, offs)
+    z0, z1, fl = T.twofold_dot_batched(dev(x), dev(y), offs)
+    assert_bits(z0, r0, "z0")
+    assert_bits(z1, r1, "z1")
+    assert_flags(fl, rf, "flags")
+    f = host(fl) & 1
+    lc = np.log10(cond)
+    lo, hi = f[lc < 3.5], f[lc > 16]
+    assert lo.mean() < 0.05 and hi.mean() > 0.95
+    pl = T.plain_dot_batched(dev(x), dev(y), offs)
+    assert_bits(pl, r0, "plain twin == z0")
