@@ -1,0 +1,447 @@
+"""Benchmark of the twofold hot path on GB300.
+
+Default workload: the elementwise twofold chain z = sqrt((a*b + c)/d) over
+n = 2^28 twofolds (a, b, c: random sign x 10^U(-3,3), d: 10^U(-3,3), tails
+uniform in +-1/2 ulp), one twofold_ew launch per step.  Other workloads
+(--workload): dot (one n = 65536 dot), cond_dots (4096 ill-conditioned dots
+of 2^16 in one batched launch), horner (k in {5,10,20,30} x 2^24 points in
+one batched launch).
+
+Prints ONE JSON line on rank 0.  `value` is whole-job throughput with
+inputs resident in HBM; `e2e` is the same metric through the public API with
+inputs copied from pinned host memory and results read back every step.
+`--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+# FP64 issue rate of one GB300 SM measured with a dependent-free DFMA stream
+# (595 Gop/s on 152 SMs at 2.07 GHz = 1.89 op/clk/SM); DADD/DMUL issue at
+# 1.60 op/clk/SM.  The FP64 roofline below is this rate times SMs times the
+# SM clock sampled during the timed region.
+FP64_OPS_PER_CLK_SM = 1.89
+
+# Algorithmic unit costs (bytes and basic FP64 operations per result).
+EW_BYTES = 8 * 8 + 2 * 8 + 1            # 4 twofold inputs, twofold output, flag byte
+EW_PLAIN_BYTES = 4 * 8 + 8
+# basic ops of the chain: MTF1 8, ATF1 8, DTF1 6 (2 div), RTF1 20 (2 sqrt, 1 div), flag 1
+EW_OPS = 8 + 8 + 6 + 20 + 1
+DOT_BYTES = 16                           # dotted x_i, y_i
+DOT_OPS = 2 + 8                          # Two-Product + ATF1 per element
+HORNER_BYTES = 8 + 16 + 1                # x in, twofold out, flag
+HORNER_OPS_PER_STEP = 4 + 7              # MTF1.1 + ATF1.1
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during timing."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        clk, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                clk.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not clk:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(clk), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(clk)}
+
+
+# ----------------------------------------------------------------- timing
+
+def time_steps(step, steps, warmup, dist_on):
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if dist_on:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+# --------------------------------------------------------------- workloads
+
+def workload_ew(args, rank, world, dist_on):
+    import torch
+    import paper_1401_6235_gb300 as T
+    import synth
+    n = args.n or (1 << 28)
+    prog = T.CHAIN_SQRT_MAD_DIV
+    pin = lambda m: torch.empty(m, dtype=torch.float64).pin_memory().numpy()
+    host = synth.ew_chain(n, seed=rank, pinned=pin)
+    keys = ["a0", "a1", "b0", "b1", "c0", "c1", "d0", "d1"]
+    g = {k: torch.from_numpy(host[k]).to("cuda", non_blocking=True) for k in keys}
+    ins = [(g["a0"], g["a1"]), (g["b0"], g["b1"]), (g["c0"], g["c1"]), (g["d0"], g["d1"])]
+    out = (torch.empty(n, dtype=torch.float64, device="cuda"), torch.empty(n, dtype=torch.float64, device="cuda"),
+           torch.empty(n, dtype=torch.uint8, device="cuda"))
+    pout = torch.empty(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        T.twofold_ew(prog, ins, out=out)
+
+    def pstep():
+        T.plain_ew(prog, [h for h, _ in ins], out=pout)
+
+    with ClockSampler(args.smi_index) as cs:
+        ms = time_steps(step, args.steps, args.warmup, dist_on)
+    plain_ms = time_steps(pstep, args.steps, args.warmup, dist_on)
+
+    # end to end: pinned host -> device, kernel, device -> host every step
+    hout = [torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory(),
+            torch.empty(n, dtype=torch.uint8).pin_memory()]
+    hin = [torch.from_numpy(host[k]) for k in keys]
+
+    def e2e_step():
+        for src, k in zip(hin, keys):
+            g[k].copy_(src, non_blocking=True)
+        T.twofold_ew(prog, ins, out=out)
+        for dst, src in zip(hout, out):
+            dst.copy_(src, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 4)
+    e2e_ms = time_steps(e2e_step, e2e_steps, max(1, args.warmup // 2), dist_on)
+
+    per = ms / args.steps
+    gbs = EW_BYTES * n * world / (per * 1e-3) / 1e9
+    res = {
+        "metric": "twofold GB/s (elementwise chain sqrt((a*b+c)/d), 81 B/elt)",
+        "value": gbs, "unit": "GB/s", "ms_per_step": per,
+        "plain_ms_per_step": plain_ms / args.steps,
+        "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "mega_ops": n * world / (per * 1e-3) / 1e6,
+        "config": {"workload": "ew_chain sqrt((a*b+c)/d)", "n": n, "bytes_per_elt": EW_BYTES,
+                   "inputs": "a,b,c sign*10^U(-3,3), d 10^U(-3,3), tails U(+-1/2 ulp), seed = rank",
+                   "l2": "inputs (16 GiB) larger than L2; no flush needed",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": EW_BYTES * n * world / (e2e_ms / e2e_steps * 1e-3) / 1e9, "unit": "GB/s",
+                "ms_per_step": e2e_ms / e2e_steps,
+                "h2d_bytes_per_step": 64 * n, "d2h_bytes_per_step": 17 * n},
+        "gpu_launches": args.steps,
+        "clocks": cs.summary(),
+        "_kernel_ms": per, "_ops": EW_OPS * n, "_bytes": EW_BYTES * n,
+        "_sample": lambda: cpu_sample_ew(n),
+    }
+    return res
+
+
+def cpu_sample_ew(n):
+    import oracle as O
+    import paper_1401_6235_gb300 as T
+    import synth
+    m = min(n, 1 << 26)
+    d = synth.ew_chain(m, seed=0)
+    ins = [(d[k + "0"], d[k + "1"]) for k in "abcd"]
+    t = time.perf_counter()
+    O.ew(T.CHAIN_SQRT_MAD_DIV, ins)
+    dt = time.perf_counter() - t
+    return {"value": EW_BYTES * m / dt / 1e9, "unit": "GB/s", "cores": O.THREADS, "kind": "oracle",
+            "sample": f"first {m} elements of the chain workload (seed 0), {dt:.2f} s wall"}
+
+
+def workload_dot(args, rank, world, dist_on):
+    import torch
+    import paper_1401_6235_gb300 as T
+    import synth
+    n = args.n or 65536
+    x, y = synth.dot_uniform(n, seed=0)
+    gx, gy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ws = T.workspace(T.lib().twofold_workspace_bytes(T.KIND_DOT, n, 1, None))
+    out = (torch.empty(1, dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.float64, device="cuda"),
+           torch.empty(1, dtype=torch.uint8, device="cuda"))
+    step = lambda: T.twofold_dot(gx, gy, out=out, ws=ws)
+    with ClockSampler(args.smi_index) as cs:
+        ms = time_steps(step, args.steps, args.warmup, dist_on)
+    pout = torch.empty(1, dtype=torch.float64, device="cuda")
+    plain_ms = time_steps(lambda: T.plain_dot(gx, gy, out=pout, ws=ws), args.steps, args.warmup, dist_on)
+    hx, hy = torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()
+    hres = torch.empty(3, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        gx.copy_(hx, non_blocking=True)
+        gy.copy_(hy, non_blocking=True)
+        T.twofold_dot(gx, gy, out=out, ws=ws)
+        hres[:2].copy_(torch.cat([out[0], out[1]]), non_blocking=True)
+
+    e2e_ms = time_steps(e2e_step, args.steps, args.warmup, dist_on)
+    per = ms / args.steps
+    return {
+        "metric": "twofold dot latency (n=65536)", "value": per * 1e3, "unit": "us",
+        "higher_is_better": False, "ms_per_step": per,
+        "plain_ms_per_step": plain_ms / args.steps, "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "gbs": DOT_BYTES * n / (per * 1e-3) / 1e9,
+        "config": {"workload": "dot n=65536 uniform[-1,1] seed 0, L=256", "n": n,
+                   "l2": "input (1 MiB) L2-resident after warm-up (latency-bound workload)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_ms / args.steps * 1e3, "unit": "us", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 16},
+        "gpu_launches": args.steps, "clocks": cs.summary(),
+        "_kernel_ms": per, "_ops": DOT_OPS * n, "_bytes": DOT_BYTES * n,
+        "_sample": lambda: cpu_sample_dot(n),
+    }
+
+
+def cpu_sample_dot(n):
+    import oracle as O
+    import synth
+    x, y = synth.dot_uniform(n, seed=0)
+    reps = 200
+    t = time.perf_counter()
+    for _ in range(reps):
+        O.reduce(x, None, y, None)
+    dt = (time.perf_counter() - t) / reps
+    return {"value": dt * 1e6, "unit": "us", "cores": 1, "kind": "oracle",
+            "sample": f"the whole n={n} dot, mean of {reps} runs"}
+
+
+def workload_cond_dots(args, rank, world, dist_on):
+    import torch
+    import paper_1401_6235_gb300 as T
+    import synth
+    nj, n = 4096, 1 << 16
+    x, y, offs, exact, cond, _ = synth.cond_dots(nj, n, seed=rank)
+    gx, gy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ws = T.workspace(T.lib().twofold_workspace_bytes(T.KIND_DOT, nj * n, nj, None))
+    out = (torch.empty(nj, dtype=torch.float64, device="cuda"), torch.empty(nj, dtype=torch.float64, device="cuda"),
+           torch.empty(nj, dtype=torch.uint8, device="cuda"))
+    step = lambda: T.twofold_dot_batched(gx, gy, offs, out=out, ws=ws)
+    with ClockSampler(args.smi_index) as cs:
+        ms = time_steps(step, args.steps, args.warmup, dist_on)
+    pout = torch.empty(nj, dtype=torch.float64, device="cuda")
+    plain_ms = time_steps(lambda: T.plain_dot_batched(gx, gy, offs, out=pout, ws=ws), args.steps, args.warmup,
+                          dist_on)
+    per = ms / args.steps
+    return {
+        "metric": "batched twofold dots jobs/s (4096 x 2^16)", "value": nj * world / (per * 1e-3),
+        "unit": "jobs/s", "ms_per_step": per, "plain_ms_per_step": plain_ms / args.steps,
+        "slowdown_vs_plain": per / (plain_ms / args.steps), "gbs": DOT_BYTES * nj * n / (per * 1e-3) / 1e9,
+        "config": {"workload": "4096 ill-conditioned dots x 2^16, cond 10^U(2,30)", "n": nj * n,
+                   "l2": "inputs (4 GiB) larger than L2", "parallelism": f"replicas x{world}"},
+        "gpu_launches": args.steps, "clocks": cs.summary(),
+        "_kernel_ms": per, "_ops": DOT_OPS * nj * n, "_bytes": DOT_BYTES * nj * n, "_sample": None,
+    }
+
+
+def workload_horner(args, rank, world, dist_on):
+    import torch
+    import paper_1401_6235_gb300 as T
+    import synth
+    ks = [5, 10, 20, 30]
+    npts = args.n or (1 << 24)
+    coefs = np.concatenate([synth.binomial_coefs(k) for k in ks])
+    coff = np.concatenate([[0], np.cumsum([k + 1 for k in ks])[:-1]]).astype(np.int32)
+    x = np.concatenate([synth.horner_points(npts, seed=rank, stream=j) for j in range(len(ks))])
+    xoff = (np.arange(len(ks) + 1) * npts).astype(np.int64)
+    gc, gxx = torch.from_numpy(coefs).cuda(), torch.from_numpy(x).cuda()
+    out = (torch.empty(x.size, dtype=torch.float64, device="cuda"),
+           torch.empty(x.size, dtype=torch.float64, device="cuda"),
+           torch.empty(x.size, dtype=torch.uint8, device="cuda"))
+    step = lambda: T.twofold_horner_batched(gc, coff, ks, gxx, xoff, out=out)
+    with ClockSampler(args.smi_index) as cs:
+        ms = time_steps(step, args.steps, args.warmup, dist_on)
+    pout = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    plain_ms = time_steps(lambda: T.plain_horner_batched(gc, coff, ks, gxx, xoff, out=pout), args.steps,
+                          args.warmup, dist_on)
+    per = ms / args.steps
+    steps_total = sum(ks) * npts
+    return {
+        "metric": "batched twofold Horner points/s (k=5,10,20,30 x 2^24)", "value": x.size * world / (per * 1e-3),
+        "unit": "points/s", "ms_per_step": per, "plain_ms_per_step": plain_ms / args.steps,
+        "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "config": {"workload": "Horner (x-1)^k expanded, k in {5,10,20,30}, 2^24 points each, x~U[0.9,1.1]",
+                   "n": int(x.size), "l2": "inputs 512 MiB larger than L2", "parallelism": f"replicas x{world}"},
+        "gpu_launches": args.steps, "clocks": cs.summary(),
+        "_kernel_ms": per, "_ops": HORNER_OPS_PER_STEP * steps_total + len(ks) * npts,
+        "_bytes": HORNER_BYTES * x.size, "_sample": None,
+    }
+
+
+WORKLOADS = {"ew_chain": workload_ew, "dot": workload_dot, "cond_dots": workload_cond_dots,
+             "horner": workload_horner}
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, on a bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle as O
+    import paper_1401_6235_gb300 as T
+    import synth
+    m = args.n or (1 << 23)
+    d = synth.ew_chain(m, seed=0)
+    ins = [(d[k + "0"], d[k + "1"]) for k in "abcd"]
+    for _ in range(args.warmup):
+        O.ew(T.CHAIN_SQRT_MAD_DIV, ins)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        O.ew(T.CHAIN_SQRT_MAD_DIV, ins)
+    dt = (time.perf_counter() - t) / args.steps
+    v = EW_BYTES * m / dt / 1e9
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "twofold GB/s (elementwise chain sqrt((a*b+c)/d), 81 B/elt)",
+        "value": v, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ew_chain sqrt((a*b+c)/d)", "n": m,
+                   "sample": f"{m} elements of the 2^28 workload per step (CPU oracle)"},
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": O.THREADS, "kind": "oracle",
+                         "sample": f"{m} elements per step"},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="ew_chain", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="override the problem size (testing)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    dist_on = world > 1
+    torch.cuda.set_device(local)
+    if dist_on:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    args.smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
+
+    import __graft_entry__ as entry
+    import paper_1401_6235_gb300 as T
+    entry.build() if not os.path.exists(T.LIB_PATH) else None
+
+    res = WORKLOADS[args.workload](args, rank, world, dist_on)
+    sample = res.pop("_sample")
+    kms, ops, nbytes = res.pop("_kernel_ms"), res.pop("_ops"), res.pop("_bytes")
+    if rank == 0:
+        hbm, src = measured_peaks()
+        clk = res["clocks"]["sm_mhz"] or 2070.0
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_fp64 = FP64_OPS_PER_CLK_SM * sms * clk * 1e6 / 1e12
+        achieved = ops / (kms * 1e-3) / 1e12
+        res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+                           "frac": achieved / peak_fp64, "traffic": None,
+                           "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
+                                   f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
+        res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
+        if sample is not None and not args.no_cpu_baseline:
+            res["cpu_baseline"] = sample()
+        line = {"metric": res.pop("metric"), "value": res.pop("value"), "unit": res.pop("unit"),
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": res.pop("ms_per_step"), "higher_is_better": res.pop("higher_is_better", True),
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+        line.update(res)
+        print(json.dumps(line), flush=True)
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

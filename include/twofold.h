@@ -18,7 +18,8 @@
  *    or synchronises.  Every call is asynchronous on `stream` (a
  *    cudaStream_t passed as void*; NULL is the legacy default stream).
  *  - Device data pointers must be 8-byte aligned (flags: any alignment).
- *    Lengths are element counts; n == 0 is valid.
+ *    Lengths are element counts; n == 0 is valid, and then data pointers
+ *    that would not be read or written may be NULL.
  *  - Results are deterministic and independent of launch configuration:
  *    z0, z1 and flags are bit-identical to the CPU oracle of the same
  *    operation order (NaN payloads excepted).

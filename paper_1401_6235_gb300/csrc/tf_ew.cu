@@ -129,13 +129,13 @@ extern "C" int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, i
     if (n < 0 || !in || !tfh::params_ok(p)) return TF_EINVAL;
     A.ntemp = check_prog(prog, nprog, nin, A.op, A.dst, A.a, A.b, &A.last);
     if (A.ntemp < 1) return TF_EINVAL;
+    if (n == 0) return TF_OK;     // nothing is dereferenced: pointers may be NULL
     if (!tfh::dptr_ok(out.hi) || !tfh::dptr_ok(out.lo)) return TF_EINVAL;
     for (int k = 0; k < nin; ++k) {
         if (!tfh::dptr_ok(in[k].hi) || !tfh::optr_ok(in[k].lo)) return TF_EINVAL;
         A.hi[k] = in[k].hi;
         A.lo[k] = in[k].lo;
     }
-    if (n == 0) return TF_OK;
     A.n = n; A.nprog = nprog; A.nin = nin;
     A.out_hi = out.hi; A.out_lo = out.lo; A.flags = out.flags;
     A.fc = tfh::flag_cfg(p);
@@ -154,12 +154,12 @@ extern "C" int plain_ew(const int32_t *prog, int32_t nprog, const double *const 
     if (n < 0 || !in) return TF_EINVAL;
     A.ntemp = check_prog(prog, nprog, nin, A.op, A.dst, A.a, A.b, &A.last);
     if (A.ntemp < 1) return TF_EINVAL;
+    if (n == 0) return TF_OK;
     if (!tfh::dptr_ok(out)) return TF_EINVAL;
     for (int k = 0; k < nin; ++k) {
         if (!tfh::dptr_ok(in[k])) return TF_EINVAL;
         A.in[k] = in[k];
     }
-    if (n == 0) return TF_OK;
     A.n = n; A.nprog = nprog; A.nin = nin; A.out = out;
     const size_t smem = (size_t)A.ntemp * kThreads * sizeof(double);
     if (smem > 48 * 1024 &&
