@@ -30,11 +30,11 @@ sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-# FP64 issue rate of one GB300 SM measured with a dependent-free DFMA stream
-# (595 Gop/s on 152 SMs at 2.07 GHz = 1.89 op/clk/SM); DADD/DMUL issue at
-# 1.60 op/clk/SM.  The FP64 roofline below is this rate times SMs times the
-# SM clock sampled during the timed region.
-FP64_OPS_PER_CLK_SM = 1.89
+# FP64 issue rate of one GB300 SM: the nominal 1.25 TFLOP/s FP64 of the part is
+# 2 DFMA per clock per SM on 152 SMs at 2.07 GHz (2 FLOP each); a stream of
+# independent add, mul or fma measures 1.6 op/clk/SM.  The FP64 roofline below
+# is 2 op/clk/SM times SMs times the SM clock sampled during the timed region.
+FP64_OPS_PER_CLK_SM = 2.0
 
 # Algorithmic unit costs (bytes and basic FP64 operations per result).
 EW_BYTES = 8 * 8 + 2 * 8 + 1            # 4 twofold inputs, twofold output, flag byte

@@ -1,13 +1,16 @@
 // Device-side twofold arithmetic (Latkin, "Twofold fast arithmetic").
 //
-// Every binary64 operation is an explicit round-to-nearest intrinsic
-// (__dadd_rn, __dsub_rn, __dmul_rn, __fma_rn, __ddiv_rn, __dsqrt_rn), which
-// the compiler never contracts or reassociates; the library is also built
-// with -fmad=false.  Each function performs the operations of its algorithm
-// in the paper's order, so results are bit-identical to any correct
-// implementation of the same sequence.
+// Every binary64 operation is either an explicit round-to-nearest intrinsic
+// (__dadd_rn, __dsub_rn, __dmul_rn, __fma_rn), which the compiler never
+// contracts or reassociates (the library is also built with -fmad=false), or
+// an integer-pipe routine of tf_soft.cuh that returns the same bits as the
+// IEEE operation (division, square root, the exact Two-Sum tail).  Each
+// function performs the operations of its algorithm in the paper's order, so
+// results are bit-identical to any correct implementation of the sequence.
 #pragma once
 #include <cstdint>
+
+#include "tf_soft.cuh"
 
 namespace tf {
 
@@ -23,24 +26,22 @@ __device__ __forceinline__ bool finite_bits(double v) {
 // ------------------------------------------------- Background: exact transforms
 
 // Algorithm 1.2 (Two-Sum): a + b -> s + t, t the exact rounding error.
+// s is one native addition; the tail t comes from soft::sum_err, which gives
+// the bits of steps (2)-(6) (exact error, +0 when zero, the literal sequence
+// near overflow and for Inf/NaN) on the integer pipes.
 __device__ __forceinline__ void two_sum(double a, double b, double &s, double &t) {
     s = __dadd_rn(a, b);
-    double bv = __dsub_rn(s, a);
-    double av = __dsub_rn(s, bv);
-    double br = __dsub_rn(b, bv);
-    double ar = __dsub_rn(a, av);
-    t = __dadd_rn(ar, br);
+    t = soft::sum_err(a, b, s);
 }
 
 // Algorithm 2.2 (Two-Diff): a - b -> d + t.  Steps (4),(5) in Shewchuk's
-// order (b# = b' - b, a# = a - a'), which makes a - b = d + t exact.
+// order (b# = b' - b, a# = a - a'), which makes a - b = d + t exact.  With
+// round-to-nearest every step of Two-Diff(a, b) is the negation-mirror of
+// Two-Sum(a, -b) (b' = a - d = -(d - a), a' = b' + d = d - (d - a), ...), so
+// its tail is the Two-Sum tail of (a, -b, d), bit for bit.
 __device__ __forceinline__ void two_diff(double a, double b, double &d, double &t) {
     d = __dsub_rn(a, b);
-    double bv = __dsub_rn(a, d);
-    double av = __dadd_rn(bv, d);
-    double br = __dsub_rn(bv, b);
-    double ar = __dsub_rn(a, av);
-    t = __dadd_rn(ar, br);
+    t = soft::sum_err(a, -b, d);
 }
 
 // Algorithm 3 (Two-Product-FMA): p = a*b, e = fma(a, b, -p).
@@ -49,15 +50,27 @@ __device__ __forceinline__ void two_prod(double a, double b, double &p, double &
     e = __fma_rn(a, b, -p);
 }
 
+// Correctly rounded division and square root (integer pipes, IEEE bits).
+__device__ __forceinline__ double div_rn(double a, double b) { return soft::div_rn(a, b); }
+__device__ __forceinline__ double sqrt_rn(double a) { return soft::sqrt_rn(a); }
+
+// 2 * c: an exponent increment when c is normal and 2c stays finite,
+// otherwise the native multiplication (zeros, subnormals, Inf, NaN, overflow).
+__device__ __forceinline__ double twice(double c) {
+    const uint64_t u = bits_of(c);
+    const unsigned e = (unsigned)((u >> 52) & 0x7FF);
+    return (e - 1u < 2045u) ? from_bits(u + (1ull << 52)) : __dmul_rn(2.0, c);
+}
+
 // Algorithm 4: q = a/b, r = fma(-q, b, a) = a - q b exactly.
 __device__ __forceinline__ void div_rem(double a, double b, double &q, double &r) {
-    q = __ddiv_rn(a, b);
+    q = div_rn(a, b);
     r = __fma_rn(-q, b, a);
 }
 
 // Algorithm 5: c = sqrt(a), d = fma(-c, c, a) = a - c^2 exactly.
 __device__ __forceinline__ void sqrt_rem(double a, double &c, double &d) {
-    c = __dsqrt_rn(a);
+    c = sqrt_rn(a);
     d = __fma_rn(-c, c, a);
 }
 
@@ -112,14 +125,14 @@ __device__ __forceinline__ d2 mtf11(double x0, double x1, double y0) {
 __device__ __forceinline__ d2 dtf111(double x0, double y0) {
     double q, r;
     div_rem(x0, y0, q, r);
-    return {q, __ddiv_rn(r, y0)};
+    return {q, div_rn(r, y0)};
 }
 
 // DTF1.1: z0 = x0/y0; r = fma(-z0, y0, x0); c = r + x1; z1 = c/y0.
 __device__ __forceinline__ d2 dtf11(double x0, double x1, double y0) {
     double q, r;
     div_rem(x0, y0, q, r);
-    return {q, __ddiv_rn(__dadd_rn(r, x1), y0)};
+    return {q, div_rn(__dadd_rn(r, x1), y0)};
 }
 
 // DTF1: z0 = x0/y0; r0 = fma(-z0, y0, x0); r1 = fma(-z0, y1, x1);
@@ -130,27 +143,27 @@ __device__ __forceinline__ d2 dtf1(double x0, double x1, double y0, double y1) {
     double r1 = __fma_rn(-q, y1, x1);
     double c0 = __dadd_rn(r0, r1);
     double d0 = __dadd_rn(y0, y1);
-    return {q, __ddiv_rn(c0, d0)};
+    return {q, div_rn(c0, d0)};
 }
 
 // RPF1: z0 = sqrt(x0); z1 = (x1 + fma(-z0, z0, x0)) / (2 z0).
 __device__ __forceinline__ d2 rpf1(double x0, double x1) {
     double c, d;
     sqrt_rem(x0, c, d);
-    return {c, __ddiv_rn(__dadd_rn(x1, d), __dmul_rn(2.0, c))};
+    return {c, div_rn(__dadd_rn(x1, d), twice(c))};
 }
 
 // RPF1.1: z0 = sqrt(x0); z1 = fma(-z0, z0, x0) / (2 z0).
 __device__ __forceinline__ d2 rpf11(double x0) {
     double c, d;
     sqrt_rem(x0, c, d);
-    return {c, __ddiv_rn(d, __dmul_rn(2.0, c))};
+    return {c, div_rn(d, twice(c))};
 }
 
 // RTF1: z0 = sqrt(x0); (u0,u1) = Two-Sum(x0, x1); (v0,v1) = RPF1(u0,u1);
 //       (w0,w1) = STF1.1((v0,v1), z0); z1 = w0 + w1.
 __device__ __forceinline__ d2 rtf1(double x0, double x1) {
-    double z0 = __dsqrt_rn(x0);
+    double z0 = sqrt_rn(x0);
     double u0, u1;
     two_sum(x0, x1, u0, u1);
     d2 v = rpf1(u0, u1);
@@ -221,11 +234,16 @@ __device__ __forceinline__ double ulp_of(double v) {
     return from_bits(1ull << (p + 1074));   // subnormal power of two
 }
 
+// |z1| > lim compared on the integer pipe: for non-negative non-NaN
+// binary64 values the bit patterns order like the values; a NaN on either
+// side compares false, as the floating-point comparison does.
 __device__ __forceinline__ uint8_t flag_of(double z0, double z1, const FlagCfg &f) {
     uint8_t r = 0;
     if (!finite_bits(z0) || !finite_bits(z1)) r |= 2;
-    double lim = (f.mode == 0) ? __dmul_rn(f.tau, fabs(z0)) : __dmul_rn(f.m, ulp_of(z0));
-    if (fabs(z1) > lim) r |= 1;
+    const double lim = (f.mode == 0) ? __dmul_rn(f.tau, fabs(z0)) : __dmul_rn(f.m, ulp_of(z0));
+    const uint64_t a = bits_of(z1) & 0x7FFFFFFFFFFFFFFFull, l = bits_of(lim) & 0x7FFFFFFFFFFFFFFFull;
+    const uint64_t inf = 0x7FF0000000000000ull;
+    if (a <= inf && l <= inf && a > l) r |= 1;
     return r;
 }
 

@@ -1,0 +1,306 @@
+// Correctly rounded binary64 primitives computed on the integer pipes.
+//
+// On GB300 the FP64 pipe issues about 2 operations per clock per SM while
+// the integer pipes issue about 90; a native __ddiv_rn or __dsqrt_rn costs
+// about 8.5 FP64 issue slots.  The functions below produce the SAME bits as
+// the native round-to-nearest-even operation (IEEE 754 binary64) but do the
+// work with 32/64-bit integer instructions and one single-precision seed from
+// the special-function unit:
+//
+//   div_rn(a, b)        a / b
+//   sqrt_rn(a)          sqrt(a)
+//   sum_err(a, b, s)    a + b - s exactly, for s = RN(a + b)   (Two-Sum tail)
+//
+// Each has a fast path for the ordinary case (normal operands and result)
+// and falls back to the native instruction otherwise (zeros, subnormals,
+// Inf, NaN, results near the overflow or underflow thresholds), so the
+// result is always the IEEE result.  Division and square root use the
+// classic scheme: a reciprocal (square-root reciprocal) seed, two
+// Newton-Raphson steps in 64-bit fixed point, a quotient (root) estimate
+// within one unit, and an exact integer remainder that corrects the
+// estimate and decides the rounding (Markstein-style correction; see e.g.
+// Muller et al., Handbook of Floating-Point Arithmetic, ch. 9 and 10).
+//
+// The header also compiles as plain C++ (no CUDA) so the host test suite can
+// check the integer algorithms against the CPU's IEEE operations; there the
+// seeds come from correctly rounded float operations.
+#pragma once
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+
+#if defined(__CUDACC__)
+#define TFS_HD __host__ __device__ __forceinline__
+#else
+#define TFS_HD inline
+#endif
+
+namespace tf {
+namespace soft {
+
+constexpr uint64_t kFrac = 0x000FFFFFFFFFFFFFull;
+constexpr uint64_t kHid = 0x0010000000000000ull;
+constexpr uint64_t kSign = 0x8000000000000000ull;
+
+TFS_HD uint64_t d2u(double x) {
+#if defined(__CUDA_ARCH__)
+    return (uint64_t)__double_as_longlong(x);
+#else
+    uint64_t u;
+    std::memcpy(&u, &x, 8);
+    return u;
+#endif
+}
+
+TFS_HD double u2d(uint64_t u) {
+#if defined(__CUDA_ARCH__)
+    return __longlong_as_double((long long)u);
+#else
+    double x;
+    std::memcpy(&x, &u, 8);
+    return x;
+#endif
+}
+
+TFS_HD uint64_t mulhi(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+TFS_HD int clz64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)v);
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+// Seed tests may perturb on the host: relative factor applied to seeds.
+#if !defined(__CUDA_ARCH__)
+inline float &host_seed_scale() {
+    static float s = 1.0f;
+    return s;
+}
+#endif
+
+// 1/f for f in [2^23, 2^24), relative error below 2^-22.
+TFS_HD float rcp_seed(float f) {
+#if defined(__CUDA_ARCH__)
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));
+    return r;
+#else
+    return (1.0f / f) * host_seed_scale();
+#endif
+}
+
+// 1/sqrt(f) for f in [2^22, 2^24), relative error below 2^-22.
+TFS_HD float rsqrt_seed(float f) {
+#if defined(__CUDA_ARCH__)
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));
+    return r;
+#else
+    return (1.0f / std::sqrt(f)) * host_seed_scale();
+#endif
+}
+
+TFS_HD uint32_t f2u(float f) {
+#if defined(__CUDA_ARCH__)
+    return __float_as_uint(f);
+#else
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+#endif
+}
+
+TFS_HD double native_div(double a, double b) {
+#if defined(__CUDA_ARCH__)
+    return __ddiv_rn(a, b);
+#else
+    volatile double r = a / b;
+    return r;
+#endif
+}
+
+TFS_HD double native_sqrt(double a) {
+#if defined(__CUDA_ARCH__)
+    return __dsqrt_rn(a);
+#else
+    volatile double r = std::sqrt(a);
+    return r;
+#endif
+}
+
+TFS_HD double native_add(double a, double b) {
+#if defined(__CUDA_ARCH__)
+    return __dadd_rn(a, b);
+#else
+    volatile double r = a + b;
+    return r;
+#endif
+}
+
+// A seed y = m * 2^(e-150) (m the 24-bit significand, e the biased
+// exponent) for w in (1, 2] as the fixed-point value w 2^63 = m << (e - bias);
+// a seed at or above w = 2 (shift 41) saturates to 2^64 - 1.
+TFS_HD uint64_t float_fixed(float y, int bias) {
+    const uint32_t u = f2u(y);
+    const uint64_t m = (uint64_t)((u & 0x7FFFFFu) | 0x800000u);
+    const int sh = (int)((u >> 23) & 0xFFu) - bias;
+    return sh >= 41 ? ~0ull : (m << sh);
+}
+
+// Y ~ 2^127 / mb for a 53-bit significand mb in [2^52, 2^53), i.e. 1/d in
+// 1.63 fixed point with d = mb / 2^53 in [1/2, 1); relative error < 2^-60.
+TFS_HD uint64_t recip_fixed(uint64_t mb) {
+    // seed: rcp of the top 24 bits, 2^29/mb = 2^-24/d -> Y0 = r * 2^87
+    uint64_t y = float_fixed(rcp_seed((float)(uint32_t)(mb >> 29)), 63);
+    const uint64_t dt = mb << 11;                       // d * 2^64
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const uint64_t t = mulhi(dt, y);                // d w 2^63, close to 2^63
+        const uint64_t e = 0 - t;                       // (2 - d w) 2^63, as 2^64 - t
+        const uint64_t lo = y * e, hi = mulhi(y, e);    // y e = w (2 - d w) 2^126
+        y = (hi >> 63) ? ~0ull : (hi << 1) | (lo >> 63);
+    }
+    return y;
+}
+
+// Correctly rounded a / b.
+TFS_HD double div_rn(double a, double b) {
+    const uint64_t ua = d2u(a), ub = d2u(b);
+    const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
+    const int ed = ea - eb;
+    // ordinary case: normal operands, quotient normal and finite before and
+    // after rounding (field of the result = ed + 1023 - sh lies in [1, 2045])
+    if ((unsigned)(ea - 1) >= 2046u || (unsigned)(eb - 1) >= 2046u || ed < -1021 || ed > 1022)
+        return native_div(a, b);
+    const uint64_t ma = (ua & kFrac) | kHid, mb = (ub & kFrac) | kHid;
+    const int sh = ma < mb;                              // quotient of significands < 1
+    const uint64_t y = recip_fixed(mb);
+    // q ~ floor(ma 2^(52+sh) / mb) = ma w 2^(sh-1), from (ma 2^11)(w 2^63)/2^64
+    uint64_t q = mulhi(ma << 11, y) >> (11 - sh);
+    // exact remainder of the 2^(52+sh)-scaled quotient, |r| < 2^63
+    int64_t r = (int64_t)((ma << (52 + sh)) - q * mb);
+    if (r < 0) { q -= 1; r += (int64_t)mb; }
+    if (r < 0) { q -= 1; r += (int64_t)mb; }
+    if ((uint64_t)r >= mb) { q += 1; r -= (int64_t)mb; }
+    if ((uint64_t)r >= mb) { q += 1; r -= (int64_t)mb; }
+    // round to nearest, ties to even (2r == mb cannot occur for binary64
+    // significands, but the rule is kept complete)
+    const uint64_t r2 = (uint64_t)r << 1;
+    q += (r2 > mb) | ((r2 == mb) & (q & 1));
+    const uint64_t sign = (ua ^ ub) & kSign;
+    return u2d(sign | (((uint64_t)(ed + 1022 - sh) << 52) + q));
+}
+
+// Correctly rounded sqrt(a).
+TFS_HD double sqrt_rn(double a) {
+    const uint64_t u = d2u(a);
+    const int f = (int)(u >> 52);                        // sign and exponent field
+    if ((unsigned)(f - 1) >= 2046u) return native_sqrt(a);   // <= 0, subnormal, Inf, NaN
+    const uint64_t mx = (u & kFrac) | kHid;
+    const int odd = f & 1;                               // unbiased exponent even
+    const int s = odd ? 52 : 53;
+    // M = mx 2^s in [2^104, 2^106); Q = floor(sqrt(M)) in [2^52, 2^53)
+    const uint64_t m_hi = mx >> (64 - s), m_lo = mx << s;
+    const uint64_t mt = (m_hi << 22) | (m_lo >> 42);     // m 2^64, m = M / 2^106 in [1/4, 1)
+    // w = 1/sqrt(m) in (1, 2] as Y = w 2^63; seed rsqrt(mt / 2^40) = w 2^-12
+    uint64_t y = float_fixed(rsqrt_seed((float)(uint32_t)(mt >> 40)), 75);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const uint64_t w2 = mulhi(y, y);                 // w^2 2^62
+        const uint64_t t = mulhi(mt, w2);                // m w^2 2^62, close to 2^62
+        const uint64_t e = 0xC000000000000000ull - t;    // (3 - m w^2) 2^62, close to 2^63
+        const uint64_t lo = y * e, hi = mulhi(y, e);     // w (3 - m w^2) 2^125
+        y = (hi >> 63) ? ~0ull : (hi << 1) | (lo >> 63); // w' 2^63, w' = w (3 - m w^2)/2
+    }
+    // sqrt(M) = m w 2^53 ~ mulhi(mt, y) / 2^10
+    uint64_t q = mulhi(mt, y) >> 10;
+    int64_t r = (int64_t)(m_lo - q * q);                 // M - q^2, exact: |r| < 2^60
+    if (r < 0) { q -= 1; r += (int64_t)(2 * q + 1); }
+    if (r < 0) { q -= 1; r += (int64_t)(2 * q + 1); }
+    if (r > (int64_t)(2 * q)) { r -= (int64_t)(2 * q + 1); q += 1; }
+    if (r > (int64_t)(2 * q)) { r -= (int64_t)(2 * q + 1); q += 1; }
+    // round to nearest: up iff M > (q + 1/2)^2, i.e. r > q (no ties exist)
+    q += (uint64_t)(r > (int64_t)q);
+    const int fr = (f + 1022 + odd) >> 1;                // biased exponent of the root
+    return u2d(((uint64_t)(fr - 1) << 52) + q);
+}
+
+// Signed integer significand m and scale q of a finite x = m 2^q.
+TFS_HD void unpack(uint64_t u, int64_t &m, int &q) {
+    const int e = (int)((u >> 52) & 0x7FF);
+    const uint64_t f = (u & kFrac) | (e ? kHid : 0);
+    q = (e ? e : 1) - 1075;
+    m = (u >> 63) ? -(int64_t)f : (int64_t)f;
+}
+
+// m 2^sh modulo 2^64 for 0 <= sh; a shift of 64 or more gives 0.
+TFS_HD uint64_t shl_mod(int64_t m, int sh) { return sh >= 64 ? 0 : ((uint64_t)m << sh); }
+
+// The tail of Algorithm 1.2 (Two-Sum) by its six native operations.
+TFS_HD double literal_sum_err(double a, double b, double s) {
+#if defined(__CUDA_ARCH__)
+    const double bv = __dsub_rn(s, a), av = __dsub_rn(s, bv);
+    return __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+#else
+    volatile double bv = s - a;
+    volatile double av = s - bv;
+    volatile double ar = a - av;
+    volatile double br = b - bv;
+    volatile double t = ar + br;
+    return t;
+#endif
+}
+
+// t = a + b - s exactly, where s = RN(a + b): bit-identical to the tail of
+// Algorithm 1.2 (Two-Sum), whose result is +0 when the error is zero.  When
+// both operands are below 2^1022 in magnitude no intermediate of the
+// literal sequence can overflow and its tail is the exact error; otherwise
+// (near-overflow operands, Inf, NaN) the literal sequence runs natively.
+// All three of a, b, s are integer multiples of 2^qmin, the finer of the two
+// operands' ulps, and |t| <= ulp(s)/2, so the integer A + B - S is small and
+// is formed modulo 2^64 when the exponent gap is at most 60.  With a larger
+// gap the smaller operand is below a quarter ulp of the larger: s is the
+// larger operand and t the smaller one.
+TFS_HD double sum_err(double a, double b, double s) {
+    const uint64_t ua = d2u(a), ub = d2u(b), us = d2u(s);
+    if ((((ua >> 52) & 0x7FF) >= 2045) | (((ub >> 52) & 0x7FF) >= 2045))
+        return literal_sum_err(a, b, s);
+    int64_t ma, mb, ms;
+    int qa, qb, qs;
+    unpack(ua, ma, qa);
+    unpack(ub, mb, qb);
+    unpack(us, ms, qs);
+    const int qmin = qa < qb ? qa : qb;
+    const int gap = (qa > qb ? qa : qb) - qmin;
+    if (gap > 60) {
+        // t = the operand with the finer ulp (never -0: a zero error is +0)
+        const uint64_t small = qa < qb ? ua : ub;
+        return u2d((small << 1) ? small : 0);
+    }
+    int64_t big = (int64_t)(shl_mod(ma, qa - qmin) + shl_mod(mb, qb - qmin));
+    // s is a multiple of 2^qmin; its own scale may be finer when the sum cancels
+    const int ds = qs - qmin;
+    int64_t sv = ds >= 0 ? (int64_t)shl_mod(ms, ds) : (ms >> (-ds));
+    const int64_t t = big - sv;
+    if (t == 0) return 0.0;
+    const uint64_t sign = t < 0 ? kSign : 0;
+    const uint64_t mag = (uint64_t)(t < 0 ? -t : t);
+    const int lz = clz64(mag);
+    const int lead = 63 - lz + qmin;                     // exponent of the leading bit
+    if (lead >= -1022) {
+        const uint64_t frac = ((mag << lz) >> 11) & kFrac;   // exact: t fits 53 bits
+        return u2d(sign | ((uint64_t)(lead + 1023) << 52) | frac);
+    }
+    return u2d(sign | (mag << (qmin + 1074)));          // subnormal tail
+}
+
+}  // namespace soft
+}  // namespace tf

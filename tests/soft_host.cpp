@@ -1,0 +1,172 @@
+// Host build of the library's integer binary64 primitives (tf_soft.cuh),
+// checked in bulk against the CPU's own IEEE operations and against the
+// literal Two-Sum sequence.  Test infrastructure: compiled by
+// tests/test_soft_primitives.py with g++ -ffp-contract=off.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "../paper_1401_6235_gb300/csrc/tf_soft.cuh"
+
+using namespace tf::soft;
+
+namespace {
+
+uint64_t mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// random double: exponent field uniform in [elo, ehi], random sign/fraction
+double rnd(uint64_t key, uint64_t i, int elo, int ehi) {
+    uint64_t r = mix(key + (i + 1) * 0x9E3779B97F4A7C15ULL);
+    uint64_t r2 = mix(r ^ 0xD1B54A32D192ED03ULL);
+    int e = elo + (int)(r2 % (uint64_t)(ehi - elo + 1));
+    uint64_t f = r & kFrac;
+    // bias towards edge significands now and then
+    switch ((r2 >> 20) & 15) {
+    case 0: f = 0; break;
+    case 1: f = kFrac; break;
+    case 2: f &= 0xFFFF000000000000ull >> 12; break;
+    case 3: f |= 0x000FFFFFFF000000ull; break;
+    default: break;
+    }
+    return u2d(((r2 >> 63) << 63) | ((uint64_t)e << 52) | f);
+}
+
+bool same(double x, double y) {
+    if (std::isnan(x) || std::isnan(y)) return std::isnan(x) && std::isnan(y);
+    return d2u(x) == d2u(y);
+}
+
+double literal_two_sum_tail(double a, double b) {
+    volatile double s = a + b;
+    volatile double bv = s - a;
+    volatile double av = s - bv;
+    volatile double br = b - bv;
+    volatile double ar = a - av;
+    volatile double t = ar + br;
+    return t;
+}
+
+double literal_two_diff_tail(double a, double b) {
+    volatile double d = a - b;
+    volatile double bv = a - d;
+    volatile double av = bv + d;
+    volatile double br = bv - b;
+    volatile double ar = a - av;
+    volatile double t = ar + br;
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+void set_seed_scale(float s) { host_seed_scale() = s; }
+
+double soft_div(double a, double b) { return div_rn(a, b); }
+double soft_sqrt(double a) { return sqrt_rn(a); }
+double soft_sum_err(double a, double b) { return sum_err(a, b, native_add(a, b)); }
+
+// Mismatch counts over n random cases; the first bad pair goes to bad[0..1].
+int64_t check_div(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
+        volatile double ref = a / b;
+        if (!same(div_rn(a, b), ref)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+int64_t check_sqrt(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = std::fabs(rnd(key, i, elo, ehi));
+        volatile double ref = std::sqrt(a);
+        if (!same(sqrt_rn(a), ref)) {
+            if (!nbad) bad[0] = a;
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+// Two-Sum tail: exponents of a and b drawn independently in [elo, ehi]
+// (gaps of any size), compared with the literal six-operation sequence.
+int64_t check_sum_err(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
+        if (i & 1) b = -a * (1.0 + std::ldexp((double)(i % 97), -50));   // heavy cancellation
+        if (i % 5 == 0) b = std::ldexp(a, -(int)(i % 70));                 // controlled gaps
+        double ref = literal_two_sum_tail(a, b);
+        double got = sum_err(a, b, native_add(a, b));
+        if (!same(got, ref)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+// Two-Diff tail (Shewchuk's order) equals the Two-Sum tail of (a, -b, a - b).
+int64_t check_diff_err(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
+        if (i & 1) b = a * (1.0 + std::ldexp((double)(i % 97), -50));
+        if (i % 5 == 0) b = std::ldexp(a, -(int)(i % 70));
+        volatile double d = a - b;
+        double ref = literal_two_diff_tail(a, b);
+        double got = sum_err(a, -b, d);
+        if (!same(got, ref)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+// Quotients near rounding boundaries: b random, q a random double, a the
+// product q*b rounded, nudged by a few ulps.
+int64_t check_div_hard(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double b = rnd(key, 2 * i, 1000, 1046), q = rnd(key, 2 * i + 1, 1000, 1046);
+        double a = q * b;
+        uint64_t ua = d2u(a) + (int64_t)(i % 7) - 3;
+        a = u2d(ua);
+        volatile double ref = a / b;
+        if (!same(div_rn(a, b), ref)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+// Perfect squares and their neighbours.
+int64_t check_sqrt_hard(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = std::fabs(rnd(key, i, 500, 1500));
+        double a = r * r;
+        if (!(a > 0) || std::isinf(a)) continue;
+        uint64_t ua = d2u(a) + (int64_t)(i % 5) - 2;
+        a = u2d(ua);
+        volatile double ref = std::sqrt(a);
+        if (!same(sqrt_rn(a), ref)) {
+            if (!nbad) bad[0] = a;
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+}  // extern "C"
