@@ -54,13 +54,8 @@ __device__ __forceinline__ void two_prod(double a, double b, double &p, double &
 __device__ __forceinline__ double div_rn(double a, double b) { return soft::div_rn(a, b); }
 __device__ __forceinline__ double sqrt_rn(double a) { return soft::sqrt_rn(a); }
 
-// 2 * c: an exponent increment when c is normal and 2c stays finite,
-// otherwise the native multiplication (zeros, subnormals, Inf, NaN, overflow).
-__device__ __forceinline__ double twice(double c) {
-    const uint64_t u = bits_of(c);
-    const unsigned e = (unsigned)((u >> 52) & 0x7FF);
-    return (e - 1u < 2045u) ? from_bits(u + (1ull << 52)) : __dmul_rn(2.0, c);
-}
+// 2 * c with IEEE bits, in integer form (soft::twice).
+__device__ __forceinline__ double twice(double c) { return soft::twice(c); }
 
 // Algorithm 4: q = a/b, r = fma(-q, b, a) = a - q b exactly.
 __device__ __forceinline__ void div_rem(double a, double b, double &q, double &r) {

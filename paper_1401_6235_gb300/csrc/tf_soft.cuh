@@ -178,8 +178,18 @@ TFS_HD double div_rn(double a, double b) {
     const int ed = ea - eb;
     // ordinary case: normal operands, quotient normal and finite before and
     // after rounding (field of the result = ed + 1023 - sh lies in [1, 2045])
-    if ((unsigned)(ea - 1) >= 2046u || (unsigned)(eb - 1) >= 2046u || ed < -1021 || ed > 1022)
+    if ((unsigned)(ea - 1) >= 2046u || (unsigned)(eb - 1) >= 2046u || ed < -1021 || ed > 1022) {
+        // IEEE special cases in integer form (no native instruction, so
+        // lanes holding NaN or Inf do not make the whole warp run one);
+        // subnormal operands and quotients near the range limits go native.
+        const uint64_t xa = ua & ~kSign, xb = ub & ~kSign, inf = 0x7FF0000000000000ull;
+        const uint64_t sign = (ua ^ ub) & kSign;
+        if (xa > inf || xb > inf || (xa == inf && xb == inf) || (xa == 0 && xb == 0))
+            return u2d(0x7FF8000000000000ull);
+        if (xa == inf || xb == 0) return u2d(sign | inf);
+        if (xa == 0 || xb == inf) return u2d(sign);
         return native_div(a, b);
+    }
     const uint64_t ma = (ua & kFrac) | kHid, mb = (ub & kFrac) | kHid;
     const int sh = ma < mb;                              // quotient of significands < 1
     const uint64_t y = recip_fixed(mb);
@@ -203,7 +213,13 @@ TFS_HD double div_rn(double a, double b) {
 TFS_HD double sqrt_rn(double a) {
     const uint64_t u = d2u(a);
     const int f = (int)(u >> 52);                        // sign and exponent field
-    if ((unsigned)(f - 1) >= 2046u) return native_sqrt(a);   // <= 0, subnormal, Inf, NaN
+    if ((unsigned)(f - 1) >= 2046u) {
+        // IEEE special cases in integer form; positive subnormals go native
+        if ((u << 1) == 0) return a;                           // sqrt(+-0) = +-0
+        if (u >> 63) return u2d(0x7FF8000000000000ull);        // negative or -NaN
+        if (f == 0x7FF) return a;                              // +Inf, +NaN
+        return native_sqrt(a);
+    }
     const uint64_t mx = (u & kFrac) | kHid;
     const int odd = f & 1;                               // unbiased exponent even
     const int s = odd ? 52 : 53;
@@ -231,6 +247,20 @@ TFS_HD double sqrt_rn(double a) {
     q += (uint64_t)(r > (int64_t)q);
     const int fr = (f + 1022 + odd) >> 1;                // biased exponent of the root
     return u2d(((uint64_t)(fr - 1) << 52) + q);
+}
+
+// 2 * c exactly as the IEEE multiplication, in integer form: an exponent
+// increment for normal c, a doubled significand for subnormal c (which may
+// carry into the smallest normal exponent), Inf from the top binade, and Inf,
+// NaN and zeros unchanged.
+TFS_HD double twice(double c) {
+    const uint64_t u = d2u(c);
+    const unsigned e = (unsigned)((u >> 52) & 0x7FF);
+    const uint64_t sign = u & kSign;
+    if (e - 1u < 2045u) return u2d(u + (1ull << 52));
+    if (e == 0) return u2d(sign | ((u & kFrac) << 1));
+    if (e == 2046) return u2d(sign | 0x7FF0000000000000ull);
+    return c;
 }
 
 // Signed integer significand m and scale q of a finite x = m 2^q.
@@ -271,8 +301,12 @@ TFS_HD double literal_sum_err(double a, double b, double s) {
 // larger operand and t the smaller one.
 TFS_HD double sum_err(double a, double b, double s) {
     const uint64_t ua = d2u(a), ub = d2u(b), us = d2u(s);
-    if ((((ua >> 52) & 0x7FF) >= 2045) | (((ub >> 52) & 0x7FF) >= 2045))
+    const unsigned fa = (unsigned)((ua >> 52) & 0x7FF), fb = (unsigned)((ub >> 52) & 0x7FF);
+    if ((fa >= 2045) | (fb >= 2045)) {
+        // an Inf or NaN operand makes every variant of the literal sequence NaN
+        if ((fa == 0x7FF) | (fb == 0x7FF)) return u2d(0x7FF8000000000000ull);
         return literal_sum_err(a, b, s);
+    }
     int64_t ma, mb, ms;
     int qa, qb, qs;
     unpack(ua, ma, qa);

@@ -70,6 +70,19 @@ double soft_div(double a, double b) { return div_rn(a, b); }
 double soft_sqrt(double a) { return sqrt_rn(a); }
 double soft_sum_err(double a, double b) { return sum_err(a, b, native_add(a, b)); }
 
+int64_t check_twice(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double c = rnd(key, i, elo, ehi);
+        volatile double ref = 2.0 * c;
+        if (!same(twice(c), ref)) {
+            if (!nbad) bad[0] = c;
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 // Mismatch counts over n random cases; the first bad pair goes to bad[0..1].
 int64_t check_div(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
     int64_t nbad = 0;

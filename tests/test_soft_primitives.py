@@ -19,7 +19,7 @@ def H(tmp_path_factory):
                            "-shared", os.path.join(HERE, "soft_host.cpp"), "-o", str(so)])
     L = ctypes.CDLL(str(so))
     d, i64, u64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
-    for name in ("check_div", "check_sqrt", "check_sum_err", "check_diff_err"):
+    for name in ("check_div", "check_sqrt", "check_sum_err", "check_diff_err", "check_twice"):
         getattr(L, name).argtypes = [u64, i64, ctypes.c_int, ctypes.c_int, p]
         getattr(L, name).restype = i64
     for name in ("check_div_hard", "check_sqrt_hard"):
@@ -79,6 +79,12 @@ def test_diff_err_matches_literal_two_diff(H):
     run(H, "check_diff_err", 13, 2_000_000, 900, 1150)
     run(H, "check_diff_err", 14, 1_000_000, 0, 2047)
     run(H, "check_diff_err", 15, 1_000_000, 1980, 2046)
+
+
+def test_twice_matches_ieee(H):
+    run(H, "check_twice", 16, 1_000_000, 0, 2047)
+    run(H, "check_twice", 17, 200_000, 0, 2)
+    run(H, "check_twice", 18, 200_000, 2044, 2047)
 
 
 def test_corner_values(H):
