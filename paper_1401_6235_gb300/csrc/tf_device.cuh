@@ -41,7 +41,7 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &t
 // its tail is the Two-Sum tail of (a, -b, d), bit for bit.
 __device__ __forceinline__ void two_diff(double a, double b, double &d, double &t) {
     d = __dsub_rn(a, b);
-    t = soft::sum_err(a, -b, d);
+    t = soft::sum_err(a, from_bits(bits_of(b) ^ 0x8000000000000000ull), d);   // -b by its sign bit
 }
 
 // Algorithm 3 (Two-Product-FMA): p = a*b, e = fma(a, b, -p).
@@ -116,43 +116,56 @@ __device__ __forceinline__ d2 mtf11(double x0, double x1, double y0) {
     return {p00, __dadd_rn(e00, __dmul_rn(x1, y0))};
 }
 
+// The divisions below share reciprocal estimates (soft::div_rn_y): both
+// divisions of DTF1.1 / DTF1.1.1 divide by y0; DTF1's second divisor
+// d0 = y0 (+) y1 usually rounds back to y0; RPF1's divisor 2 z0 has the
+// significand of z0, whose reciprocal square-root estimate the square root
+// already produced.  Every quotient is still the correctly rounded one.
+
 // DTF1.1.1: z0 = x0/y0; r1 = fma(-z0, y0, x0); z1 = r1/y0.
 __device__ __forceinline__ d2 dtf111(double x0, double y0) {
-    double q, r;
-    div_rem(x0, y0, q, r);
-    return {q, div_rn(r, y0)};
+    const uint64_t yb = soft::recip_of(y0);
+    const double q = soft::div_rn_y(x0, y0, yb);
+    const double r = __fma_rn(-q, y0, x0);
+    return {q, soft::div_rn_y(r, y0, yb)};
 }
 
 // DTF1.1: z0 = x0/y0; r = fma(-z0, y0, x0); c = r + x1; z1 = c/y0.
 __device__ __forceinline__ d2 dtf11(double x0, double x1, double y0) {
-    double q, r;
-    div_rem(x0, y0, q, r);
-    return {q, div_rn(__dadd_rn(r, x1), y0)};
+    const uint64_t yb = soft::recip_of(y0);
+    const double q = soft::div_rn_y(x0, y0, yb);
+    const double r = __fma_rn(-q, y0, x0);
+    return {q, soft::div_rn_y(__dadd_rn(r, x1), y0, yb)};
 }
 
 // DTF1: z0 = x0/y0; r0 = fma(-z0, y0, x0); r1 = fma(-z0, y1, x1);
 //       c0 = r0 + r1; d0 = y0 + y1; z1 = c0/d0.
 __device__ __forceinline__ d2 dtf1(double x0, double x1, double y0, double y1) {
-    double q, r0;
-    div_rem(x0, y0, q, r0);
-    double r1 = __fma_rn(-q, y1, x1);
-    double c0 = __dadd_rn(r0, r1);
-    double d0 = __dadd_rn(y0, y1);
-    return {q, div_rn(c0, d0)};
+    const uint64_t yb = soft::recip_of(y0);
+    const double q = soft::div_rn_y(x0, y0, yb);
+    const double r0 = __fma_rn(-q, y0, x0);
+    const double r1 = __fma_rn(-q, y1, x1);
+    const double c0 = __dadd_rn(r0, r1);
+    const double d0 = __dadd_rn(y0, y1);
+    uint64_t yd = yb;
+    if (bits_of(d0) != bits_of(y0)) yd = soft::recip_of(d0);
+    return {q, soft::div_rn_y(c0, d0, yd)};
 }
 
 // RPF1: z0 = sqrt(x0); z1 = (x1 + fma(-z0, z0, x0)) / (2 z0).
 __device__ __forceinline__ d2 rpf1(double x0, double x1) {
-    double c, d;
-    sqrt_rem(x0, c, d);
-    return {c, div_rn(__dadd_rn(x1, d), twice(c))};
+    uint64_t y;
+    const double c = soft::sqrt_rn_y(x0, &y);
+    const double d = __fma_rn(-c, c, x0);
+    return {c, soft::div_rn_y(__dadd_rn(x1, d), twice(c), y)};
 }
 
 // RPF1.1: z0 = sqrt(x0); z1 = fma(-z0, z0, x0) / (2 z0).
 __device__ __forceinline__ d2 rpf11(double x0) {
-    double c, d;
-    sqrt_rem(x0, c, d);
-    return {c, div_rn(d, twice(c))};
+    uint64_t y;
+    const double c = soft::sqrt_rn_y(x0, &y);
+    const double d = __fma_rn(-c, c, x0);
+    return {c, soft::div_rn_y(d, twice(c), y)};
 }
 
 // RTF1: z0 = sqrt(x0); (u0,u1) = Two-Sum(x0, x1); (v0,v1) = RPF1(u0,u1);
@@ -235,7 +248,8 @@ __device__ __forceinline__ double ulp_of(double v) {
 __device__ __forceinline__ uint8_t flag_of(double z0, double z1, const FlagCfg &f) {
     uint8_t r = 0;
     if (!finite_bits(z0) || !finite_bits(z1)) r |= 2;
-    const double lim = (f.mode == 0) ? __dmul_rn(f.tau, fabs(z0)) : __dmul_rn(f.m, ulp_of(z0));
+    const double az0 = from_bits(bits_of(z0) & 0x7FFFFFFFFFFFFFFFull);   // |z0| by its sign bit
+    const double lim = (f.mode == 0) ? __dmul_rn(f.tau, az0) : __dmul_rn(f.m, ulp_of(z0));
     const uint64_t a = bits_of(z1) & 0x7FFFFFFFFFFFFFFFull, l = bits_of(lim) & 0x7FFFFFFFFFFFFFFFull;
     const uint64_t inf = 0x7FF0000000000000ull;
     if (a <= inf && l <= inf && a > l) r |= 1;

@@ -65,6 +65,62 @@ __global__ void __launch_bounds__(kThreads) ew_kernel(const __grid_constant__ Ew
     }
 }
 
+// Chain programs: every instruction after the first takes the previous
+// result as its first operand and an input (or nothing, for SQRT) as its
+// second.  The running twofold stays in registers; no shared memory.
+struct ChainArgs {
+    int64_t n;
+    int nsteps;
+    int first;                                  // input register of the first operand
+    int8_t op[TF_EW_MAX_PROG], in[TF_EW_MAX_PROG];   // second operand's input register
+    const double *hi[TF_EW_MAX_INPUTS];
+    const double *lo[TF_EW_MAX_INPUTS];
+    double *out_hi, *out_lo;
+    uint8_t *flags;
+    tf::FlagCfg fc;
+};
+
+__global__ void __launch_bounds__(kThreads) chain_kernel(const __grid_constant__ ChainArgs A) {
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * kThreads) {
+        double x0 = A.hi[A.first][i], x1 = 0.0;
+        bool xd = A.lo[A.first] == nullptr;
+        if (!xd) x1 = A.lo[A.first][i];
+        for (int s = 0; s < A.nsteps; ++s) {
+            const int op = A.op[s];
+            double y0 = 0.0, y1 = 0.0;
+            bool yd = true;
+            if (op != tf::OP_SQRT) {
+                const int k = A.in[s];
+                y0 = A.hi[k][i];
+                yd = A.lo[k] == nullptr;
+                if (!yd) y1 = A.lo[k][i];
+            }
+            const tf::d2 z = tf::apply(op, x0, x1, xd, y0, y1, yd);
+            x0 = z.z0;
+            x1 = z.z1;
+            xd = false;
+        }
+        A.out_hi[i] = x0;
+        A.out_lo[i] = x1;
+        if (A.flags) A.flags[i] = tf::flag_of(x0, x1, A.fc);
+    }
+}
+
+// A validated program in chain form: fills op/in/first and returns true.
+bool as_chain(const int8_t *op, const int8_t *dst, const int8_t *a, const int8_t *b, int nprog, int nin,
+              ChainArgs &C) {
+    if (a[0] >= nin) return false;
+    C.first = a[0];
+    for (int s = 0; s < nprog; ++s) {
+        if (s > 0 && a[s] != dst[s - 1]) return false;
+        if (op[s] != TF_SQRT && b[s] >= nin) return false;
+        C.op[s] = op[s];
+        C.in[s] = op[s] == TF_SQRT ? 0 : b[s];
+    }
+    C.nsteps = nprog;
+    return true;
+}
+
 struct PlainArgs {
     int64_t n;
     int nprog, nin, ntemp, last;
@@ -139,6 +195,15 @@ extern "C" int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, i
     A.n = n; A.nprog = nprog; A.nin = nin;
     A.out_hi = out.hi; A.out_lo = out.lo; A.flags = out.flags;
     A.fc = tfh::flag_cfg(p);
+    ChainArgs C{};
+    if (as_chain(A.op, A.dst, A.a, A.b, nprog, nin, C)) {
+        C.n = n;
+        for (int k = 0; k < nin; ++k) { C.hi[k] = A.hi[k]; C.lo[k] = A.lo[k]; }
+        C.out_hi = A.out_hi; C.out_lo = A.out_lo; C.flags = A.flags; C.fc = A.fc;
+        const int grid = grid_for(n, 0, (const void *)chain_kernel);
+        chain_kernel<<<grid, kThreads, 0, tfh::as_stream(stream)>>>(C);
+        return tfh::launch_status();
+    }
     const size_t smem = (size_t)A.ntemp * 2 * kThreads * sizeof(double);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(ew_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -155,7 +155,7 @@ TFS_HD uint64_t float_fixed(float y, int bias) {
     return sh >= 41 ? ~0ull : (m << sh);
 }
 
-// Y ~ 2^127 / mb for a 53-bit significand mb in [2^52, 2^53), i.e. 1/d in
+// Y ~ 2^116 / mb for a 53-bit significand mb in [2^52, 2^53), i.e. 1/d in
 // 1.63 fixed point with d = mb / 2^53 in [1/2, 1); relative error < 2^-60.
 TFS_HD uint64_t recip_fixed(uint64_t mb) {
     // seed: rcp of the top 24 bits, 2^29/mb = 2^-24/d -> Y0 = r * 2^87
@@ -171,8 +171,23 @@ TFS_HD uint64_t recip_fixed(uint64_t mb) {
     return y;
 }
 
+// The significand of b in [2^52, 2^53) (meaningful for normal b only).
+TFS_HD uint64_t signif(double b) { return (d2u(b) & kFrac) | kHid; }
+
+// Reciprocal of b's significand for div_rn_y; any normal b.
+TFS_HD uint64_t recip_of(double b) { return recip_fixed(signif(b)); }
+
+// Correctly rounded a / b given y, an estimate of 2^116 / signif(b) with
+// relative error below 2^-52 (recip_of(b), or the reciprocal square root of
+// sqrt_rn_y when b is twice that root), or 0 to compute it here: the
+// quotient estimate is then within two units and the remainder corrections
+// below restore the exact quotient.
+TFS_HD double div_rn_y(double a, double b, uint64_t y_in);
+
 // Correctly rounded a / b.
-TFS_HD double div_rn(double a, double b) {
+TFS_HD double div_rn(double a, double b) { return div_rn_y(a, b, 0); }
+
+TFS_HD double div_rn_y(double a, double b, uint64_t y_in) {
     const uint64_t ua = d2u(a), ub = d2u(b);
     const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
     const int ed = ea - eb;
@@ -192,7 +207,8 @@ TFS_HD double div_rn(double a, double b) {
     }
     const uint64_t ma = (ua & kFrac) | kHid, mb = (ub & kFrac) | kHid;
     const int sh = ma < mb;                              // quotient of significands < 1
-    const uint64_t y = recip_fixed(mb);
+    uint64_t y = y_in;
+    if (!y) y = recip_fixed(mb);
     // q ~ floor(ma 2^(52+sh) / mb) = ma w 2^(sh-1), from (ma 2^11)(w 2^63)/2^64
     uint64_t q = mulhi(ma << 11, y) >> (11 - sh);
     // exact remainder of the 2^(52+sh)-scaled quotient, |r| < 2^63
@@ -209,8 +225,18 @@ TFS_HD double div_rn(double a, double b) {
     return u2d(sign | (((uint64_t)(ed + 1022 - sh) << 52) + q));
 }
 
-// Correctly rounded sqrt(a).
+// Correctly rounded sqrt(a); *y_out receives 1/sqrt(m) as w 2^63 (m the
+// normalised radicand significand), which estimates 2^116 / signif(sqrt(a))
+// within 2^-52 relative (0 when the special-value path was taken).
+TFS_HD double sqrt_rn_y(double a, uint64_t *y_out);
+
 TFS_HD double sqrt_rn(double a) {
+    uint64_t y;
+    return sqrt_rn_y(a, &y);
+}
+
+TFS_HD double sqrt_rn_y(double a, uint64_t *y_out) {
+    *y_out = 0;
     const uint64_t u = d2u(a);
     const int f = (int)(u >> 52);                        // sign and exponent field
     if ((unsigned)(f - 1) >= 2046u) {
@@ -236,6 +262,7 @@ TFS_HD double sqrt_rn(double a) {
         const uint64_t lo = y * e, hi = mulhi(y, e);     // w (3 - m w^2) 2^125
         y = (hi >> 63) ? ~0ull : (hi << 1) | (lo >> 63); // w' 2^63, w' = w (3 - m w^2)/2
     }
+    *y_out = y;
     // sqrt(M) = m w 2^53 ~ mulhi(mt, y) / 2^10
     uint64_t q = mulhi(mt, y) >> 10;
     int64_t r = (int64_t)(m_lo - q * q);                 // M - q^2, exact: |r| < 2^60

@@ -164,6 +164,44 @@ int64_t check_div_hard(uint64_t key, int64_t n, double *bad) {
     return nbad;
 }
 
+// Division by 2 sqrt(u) with the reciprocal square root that sqrt_rn_y
+// returns (as in RPF1), against the CPU's t / (2 sqrt(u)).
+int64_t check_div_by_root(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double u = std::fabs(rnd(key, 2 * i, 1, 2046));
+        double t = rnd(key, 2 * i + 1, 1, 2046);
+        if (i % 3 == 0) t = std::ldexp(t, -(int)(i % 60));
+        uint64_t y;
+        double c = sqrt_rn_y(u, &y);
+        double got = div_rn_y(t, twice(c), y);
+        volatile double c2 = std::sqrt(u);
+        volatile double w = 2.0 * c2;
+        volatile double ref = t / w;
+        if (!same(got, ref)) {
+            if (!nbad) { bad[0] = t; bad[1] = u; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+// Two divisions sharing the divisor's reciprocal (as in DTF1).
+int64_t check_div_shared(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = rnd(key, 3 * i, 900, 1150), c = rnd(key, 3 * i + 1, 800, 1150);
+        double b = rnd(key, 3 * i + 2, 900, 1150);
+        uint64_t y = recip_of(b);
+        volatile double r1 = a / b, r2 = c / b;
+        if (!same(div_rn_y(a, b, y), r1) || !same(div_rn_y(c, b, y), r2)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 // Perfect squares and their neighbours.
 int64_t check_sqrt_hard(uint64_t key, int64_t n, double *bad) {
     int64_t nbad = 0;

@@ -77,6 +77,20 @@ def test_chain_config_sizes(n):
     assert_bits(pz, r0, "plain twin == z0")
 
 
+def test_chain_kernel_equals_interpreter():
+    """The chain-form program runs in the register-resident chain kernel; the
+    same computation with a dead first instruction is not chain-shaped and
+    runs in the shared-memory interpreter: identical bits."""
+    n = 100003
+    d = synth.ew_chain(n, seed=21)
+    g = [(dev(d[k + "0"]), dev(d[k + "1"])) for k in "abcd"]
+    a = T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, g)
+    prog = [(O.ADD, 8, 0, 0)] + list(T.CHAIN_SQRT_MAD_DIV)
+    b = T.twofold_ew(prog, g)
+    for u, v in zip(a, b):
+        assert np.array_equal(host(u).view(np.uint8), host(v).view(np.uint8))
+
+
 @pytest.mark.parametrize("mode", [T.PANIC_REL, T.PANIC_ULP])
 def test_chain_flag_modes(mode):
     n = 50001

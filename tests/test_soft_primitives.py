@@ -22,7 +22,7 @@ def H(tmp_path_factory):
     for name in ("check_div", "check_sqrt", "check_sum_err", "check_diff_err", "check_twice"):
         getattr(L, name).argtypes = [u64, i64, ctypes.c_int, ctypes.c_int, p]
         getattr(L, name).restype = i64
-    for name in ("check_div_hard", "check_sqrt_hard"):
+    for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared"):
         getattr(L, name).argtypes = [u64, i64, p]
         getattr(L, name).restype = i64
     L.soft_div.argtypes = [d, d]
@@ -79,6 +79,16 @@ def test_diff_err_matches_literal_two_diff(H):
     run(H, "check_diff_err", 13, 2_000_000, 900, 1150)
     run(H, "check_diff_err", 14, 1_000_000, 0, 2047)
     run(H, "check_diff_err", 15, 1_000_000, 1980, 2046)
+
+
+@pytest.mark.parametrize("scale", SCALES)
+def test_div_with_reused_reciprocals(H, scale):
+    H.set_seed_scale(scale)
+    try:
+        run(H, "check_div_by_root", 19, 2_000_000)
+        run(H, "check_div_shared", 20, 2_000_000)
+    finally:
+        H.set_seed_scale(1.0)
 
 
 def test_twice_matches_ieee(H):
