@@ -290,6 +290,100 @@ TFS_HD double twice(double c) {
     return c;
 }
 
+TFS_HD double native_mul(double a, double b) {
+#if defined(__CUDA_ARCH__)
+    return __dmul_rn(a, b);
+#else
+    volatile double r = a * b;
+    return r;
+#endif
+}
+
+// Correctly rounded a * b.  Normal operands whose product is normal (or
+// overflows) run on the integer pipes: the 106-bit product of the
+// significands, one normalisation step, round to nearest even on the
+// guard bits plus a sticky bit; the carry of a rounded-up significand
+// propagates into the exponent (and to Inf past the top binade) by the
+// packing addition.  NaN, Inf and zero operands are resolved in integer
+// form; subnormal operands and products near the underflow threshold go
+// native.
+TFS_HD double mul_rn(double a, double b) {
+    const uint64_t ua = d2u(a), ub = d2u(b);
+    const int fa = (int)((ua >> 52) & 0x7FF), fb = (int)((ub >> 52) & 0x7FF);
+    const int e = fa + fb - 1023;                        // result field for a significand product in [1, 2)
+    const uint64_t sign = (ua ^ ub) & kSign;
+    if ((unsigned)(fa - 1) >= 2046u || (unsigned)(fb - 1) >= 2046u || e < 1 || e > 2046) {
+        const uint64_t xa = ua & ~kSign, xb = ub & ~kSign, inf = 0x7FF0000000000000ull;
+        if (xa > inf || xb > inf) return u2d(0x7FF8000000000000ull);
+        if (xa == inf || xb == inf) return u2d((xa == 0 || xb == 0) ? 0x7FF8000000000000ull : (sign | inf));
+        if (xa == 0 || xb == 0) return u2d(sign);
+        if (e > 2046 && fa != 0 && fb != 0) return u2d(sign | inf);   // product >= 2^1024
+        return native_mul(a, b);
+    }
+    const uint64_t ma = ((ua & kFrac) | kHid) << 11, mb = ((ub & kFrac) | kHid) << 11;
+    const uint64_t hi = mulhi(ma, mb), lo = ma * mb;     // product of significands << 22
+    const int top = (int)(hi >> 63);                     // product in [2, 4)
+    const int gb = 10 + top;                             // guard bits below the 53-bit significand
+    uint64_t q = hi >> gb;
+    const uint64_t rem = hi & ((1ull << gb) - 1), half = 1ull << (gb - 1);
+    q += (rem > half) | ((rem == half) & ((lo != 0) | (q & 1)));
+    const uint64_t r = ((uint64_t)(e + top - 1) << 52) + q, inf = 0x7FF0000000000000ull;
+    return u2d(sign | (r >= inf ? inf : r));            // past the top binade: Inf
+}
+
+// Correctly rounded a + b.  Normal operands run on the integer pipes: the
+// significands aligned in 64-bit words with 10 guard bits, the bits shifted
+// out of the smaller operand jammed into its lowest bit (sticky), exact
+// addition or subtraction, normalisation, round to nearest even.  An exact
+// zero sum is +0.  NaN, Inf and zero operands are resolved in integer form;
+// subnormal operands and sums that land below the normal range go native.
+TFS_HD double add_rn(double a, double b) {
+    uint64_t ua = d2u(a), ub = d2u(b);
+    uint64_t xa = ua & ~kSign, xb = ub & ~kSign;
+    const uint64_t inf = 0x7FF0000000000000ull;
+    int fa = (int)(xa >> 52), fb = (int)(xb >> 52);
+    if ((unsigned)(fa - 1) >= 2046u || (unsigned)(fb - 1) >= 2046u) {
+        if (xa > inf || xb > inf) return u2d(0x7FF8000000000000ull);
+        if (xa == inf || xb == inf) {
+            if (xa == inf && xb == inf && ((ua ^ ub) & kSign)) return u2d(0x7FF8000000000000ull);
+            return xa == inf ? a : b;
+        }
+        if (xa == 0 && xb == 0) return u2d(ua & ub);      // -0 only when both are -0
+        if (xb == 0 && fa != 0) return a;
+        if (xa == 0 && fb != 0) return b;
+        return native_add(a, b);
+    }
+    if (xa < xb) {                                       // a: the larger magnitude
+        uint64_t t = ua; ua = ub; ub = t;
+        t = xa; xa = xb; xb = t;
+        int f = fa; fa = fb; fb = f;
+    }
+    const uint64_t sign = ua & kSign;
+    const int d = fa - fb;
+    const uint64_t mbig = ((xa & kFrac) | kHid) << 10;  // leading bit at 62
+    uint64_t msml = ((xb & kFrac) | kHid) << 10;
+    if (d >= 64) msml = 1;                               // only the sticky bit remains
+    else if (d > 0) msml = (msml >> d) | (uint64_t)((msml << (64 - d)) != 0);
+    int e = fa;
+    uint64_t m;
+    if ((ua ^ ub) & kSign) {
+        m = mbig - msml;
+        if (m == 0) return 0.0;
+        const int lz = clz64(m) - 1;                     // shift the leading bit back to 62
+        e -= lz;
+        if (e < 1) return native_add(a, b);              // result below the normal range
+        m <<= lz;
+    } else {
+        m = mbig + msml;
+        if (m >> 63) { m = (m >> 1) | (m & 1); e += 1; }
+    }
+    uint64_t q = m >> 10;
+    const uint64_t rem = m & 0x3FF;
+    q += (rem > 0x200) | ((rem == 0x200) & (q & 1));
+    const uint64_t r = ((uint64_t)(e - 1) << 52) + q;   // may carry to the Inf pattern
+    return u2d(sign | (r >= inf ? inf : r));
+}
+
 // Signed integer significand m and scale q of a finite x = m 2^q.
 TFS_HD void unpack(uint64_t u, int64_t &m, int &q) {
     const int e = (int)((u >> 52) & 0x7FF);

@@ -202,6 +202,35 @@ int64_t check_div_shared(uint64_t key, int64_t n, double *bad) {
     return nbad;
 }
 
+int64_t check_mul(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
+        volatile double ref = a * b;
+        if (!same(mul_rn(a, b), ref)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+int64_t check_add(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
+        if (i % 3 == 1) b = -a * (1.0 + std::ldexp((double)(i % 97), -52));   // cancellation
+        if (i % 5 == 0) b = std::ldexp(a, -(int)(i % 70));                     // controlled gaps
+        if (i % 7 == 0) b = -std::ldexp(a, -(int)(i % 66));
+        volatile double ref = a + b;
+        if (!same(add_rn(a, b), ref)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 // Perfect squares and their neighbours.
 int64_t check_sqrt_hard(uint64_t key, int64_t n, double *bad) {
     int64_t nbad = 0;

@@ -19,7 +19,8 @@ def H(tmp_path_factory):
                            "-shared", os.path.join(HERE, "soft_host.cpp"), "-o", str(so)])
     L = ctypes.CDLL(str(so))
     d, i64, u64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
-    for name in ("check_div", "check_sqrt", "check_sum_err", "check_diff_err", "check_twice"):
+    for name in ("check_div", "check_sqrt", "check_sum_err", "check_diff_err", "check_twice", "check_mul",
+                 "check_add"):
         getattr(L, name).argtypes = [u64, i64, ctypes.c_int, ctypes.c_int, p]
         getattr(L, name).restype = i64
     for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared"):
@@ -89,6 +90,20 @@ def test_div_with_reused_reciprocals(H, scale):
         run(H, "check_div_shared", 20, 2_000_000)
     finally:
         H.set_seed_scale(1.0)
+
+
+def test_mul_matches_ieee(H):
+    run(H, "check_mul", 21, 2_000_000, 900, 1150)
+    run(H, "check_mul", 22, 1_000_000, 0, 2047)
+    run(H, "check_mul", 23, 500_000, 400, 640)       # products near the underflow threshold
+    run(H, "check_mul", 24, 500_000, 1500, 1550)     # products near the overflow threshold
+
+
+def test_add_matches_ieee(H):
+    run(H, "check_add", 25, 3_000_000, 900, 1150)
+    run(H, "check_add", 26, 1_000_000, 0, 2047)
+    run(H, "check_add", 27, 500_000, 0, 60)          # subnormal and tiny
+    run(H, "check_add", 28, 500_000, 2000, 2046)     # near overflow
 
 
 def test_twice_matches_ieee(H):
