@@ -187,6 +187,20 @@ int plain_dot(const double *x, const double *y, int64_t n, double *out1, const t
 int plain_dot_batched(const double *x, const double *y, const int64_t *offs, int32_t njobs,
                       double *out, const tf_params *p, void *ws, size_t ws_bytes, void *stream);
 
+/* Dot product that allocates nothing and takes no workspace (the paper has
+ * no counterpart: this is an interface for callers that cannot provide
+ * device memory at the call, e.g. code that must not touch the allocator
+ * once running or that has no spare buffer to lend).  Same arguments,
+ * order and results as twofold_dot without ws.  Its scratch is a static
+ * 512 KiB device array of the library (up to 32768 reduction blocks, about
+ * 2^31 elements at the default leaf of 256), held on every GPU that loads
+ * the library until exit; larger requests return TF_EUNSUPPORTED before any
+ * launch.  The first call on a device looks up the array's address with
+ * cudaGetSymbolAddress (make it before any stream capture).  All calls
+ * share the array: calls that overlap on the GPU race; calls ordered on one
+ * stream do not. */
+int twofold_dot_noalloc(tf_in x, tf_in y, int64_t n, tf_out out1, const tf_params *p, void *stream);
+
 /* -------------------------------------------------------------- Horner
  *
  * p(x) = a_0 + a_1 x + ... + a_k x^k with dotted coefficients (ascending)

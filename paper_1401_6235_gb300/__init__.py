@@ -69,6 +69,7 @@ SIGNATURES = {
     "plain_sum": ([_P, _I64, _P, _PP, _P, _SZ, _P], ctypes.c_int),
     "plain_dot": ([_P, _P, _I64, _P, _PP, _P, _SZ, _P], ctypes.c_int),
     "plain_dot_batched": ([_P, _P, _P, _I32, _P, _PP, _P, _SZ, _P], ctypes.c_int),
+    "twofold_dot_noalloc": ([_IN, _IN, _I64, _OUT, _PP, _P], ctypes.c_int),
     "twofold_horner": ([_P, _I32, _P, _I64, _OUT, _PP, _P], ctypes.c_int),
     "twofold_horner_workspace_bytes": ([_I32], _SZ),
     "twofold_horner_batched": ([_P, _P, _P, _I32, _P, _P, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
@@ -221,6 +222,20 @@ def twofold_dot(x, y, xl=None, yl=None, out=None, p: tf_params | None = None, ws
     _check(lib().twofold_dot(tf_in(_dev(x), _dev(xl)), tf_in(_dev(y), _dev(yl)), n,
                              tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws), ws.numel(),
                              _stream(stream)), "twofold_dot")
+    return hi, lo, fl
+
+
+def twofold_dot_noalloc(x, y, xl=None, yl=None, out=None, p: tf_params | None = None, stream=None):
+    """twofold_dot without a workspace: the library's static device scratch
+    holds the partials (for callers that cannot allocate at the call).
+    Calls that overlap on the GPU share that scratch and race."""
+    n = x.numel()
+    if y.numel() != n:
+        raise ValueError("x and y must have the same length")
+    hi, lo, fl = _red_out(1, x.device, out)
+    _check(lib().twofold_dot_noalloc(tf_in(_dev(x), _dev(xl)), tf_in(_dev(y), _dev(yl)), n,
+                                     tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _stream(stream)),
+           "twofold_dot_noalloc")
     return hi, lo, fl
 
 

@@ -11,6 +11,7 @@
 // then an in-place strided tree in shared memory) and reduce_final
 // combines the partials of each job with the same tree.  Results therefore
 // do not depend on B, the grid or the device.
+#include <mutex>
 #include <vector>
 
 #include "tf_host.cuh"
@@ -302,4 +303,58 @@ extern "C" int plain_dot_batched(const double *x, const double *y, const int64_t
                                  double *out, const tf_params *p, void *ws, size_t ws_bytes, void *stream) {
     return run<true, true>(x, nullptr, y, nullptr, offs, njobs, out, nullptr, nullptr, p, ws, ws_bytes,
                            stream);
+}
+
+// ----------------------------------------------------------------------
+// twofold_dot_noalloc: the dot product without a caller workspace.
+//
+// For callers that cannot allocate device memory at the point of the call:
+// code that must not touch the allocator once it is running (a latency-
+// critical loop with a fixed memory budget, a plug-in inside a host program
+// that owns every device allocation), or that holds no spare buffer to lend
+// as a workspace.  The partials of the reduction live in a static device
+// array of this library, reserved on every GPU that loads it until the
+// process exits.  The array's address comes from cudaGetSymbolAddress, once
+// per device, on the first call made with that device current; make that
+// first call before any stream capture.  All calls share the one array, so
+// calls whose kernels overlap on the GPU (different streams, no ordering)
+// race; calls ordered on one stream do not.  Nothing here needs zeroing:
+// every partial is written before it is read.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 512 * 1024;   // 32768 partial blocks
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TF_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return TF_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return TF_ECUDA;
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = g_noalloc_addr[dev];
+    return TF_OK;
+}
+
+}  // namespace
+
+extern "C" int twofold_dot_noalloc(tf_in x, tf_in y, int64_t n, tf_out out1, const tf_params *p,
+                                   void *stream) {
+    if (n < 0) return TF_EINVAL;
+    void *scratch = nullptr;
+    const int st = noalloc_scratch(&scratch);
+    if (st != TF_OK) return st;
+    const int64_t offs[2] = {0, n};
+    const int r = run<true, false>(x.hi, x.lo, y.hi, y.lo, offs, 1, out1.hi, out1.lo, out1.flags, p, scratch,
+                                   kNoAllocScratchBytes, stream);
+    return r == TF_ENOSPC ? TF_EUNSUPPORTED : r;     // beyond the static scratch
 }
