@@ -71,8 +71,8 @@ enum { TF_FLAG_PANIC = 1, TF_FLAG_NONFINITE = 2 };
 typedef struct {
     int32_t panic_mode;   /* TF_PANIC_REL or TF_PANIC_ULP                      */
     int32_t leaf;         /* leaf length L of sum/dot (>= 1); default 256      */
-    double  panic_tau;    /* REL threshold, default 0x1p-40                    */
-    double  panic_ulps;   /* ULP threshold m, default 4096                     */
+    double  panic_tau;    /* REL threshold >= 0, default 0x1p-40               */
+    double  panic_ulps;   /* ULP threshold m >= 0, default 4096                */
 } tf_params;              /* a NULL tf_params* means all defaults              */
 
 typedef enum {

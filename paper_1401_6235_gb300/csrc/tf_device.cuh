@@ -41,7 +41,8 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &t
 // its tail is the Two-Sum tail of (a, -b, d), bit for bit.
 __device__ __forceinline__ void two_diff(double a, double b, double &d, double &t) {
     d = __dsub_rn(a, b);
-    t = soft::sum_err(a, from_bits(bits_of(b) ^ 0x8000000000000000ull), d);   // -b by its sign bit
+    // -b by its sign bit, handed over as a bit pattern
+    t = from_bits(soft::sum_err_bits(bits_of(a), bits_of(b) ^ 0x8000000000000000ull, bits_of(d)));
 }
 
 // Algorithm 3 (Two-Product-FMA): p = a*b, e = fma(a, b, -p).
@@ -170,12 +171,17 @@ __device__ __forceinline__ d2 rpf11(double x0) {
 
 // RTF1: z0 = sqrt(x0); (u0,u1) = Two-Sum(x0, x1); (v0,v1) = RPF1(u0,u1);
 //       (w0,w1) = STF1.1((v0,v1), z0); z1 = w0 + w1.
+// The root of u0 (a few ulps from x0) starts from the reciprocal root that
+// the root of x0 produced (soft::sqrt_rn_near; same correctly rounded bits).
 __device__ __forceinline__ d2 rtf1(double x0, double x1) {
-    double z0 = sqrt_rn(x0);
+    uint64_t yz;
+    const double z0 = soft::sqrt_rn_y(x0, &yz);
     double u0, u1;
     two_sum(x0, x1, u0, u1);
-    d2 v = rpf1(u0, u1);
-    d2 w = stf11(v.z0, v.z1, z0);
+    const double v0 = soft::sqrt_rn_near(u0, x0, yz);       // RPF1 on (u0, u1)
+    const double d = __fma_rn(-v0, v0, u0);
+    const double v1 = soft::div_rn(__dadd_rn(u1, d), twice(v0));
+    const d2 w = stf11(v0, v1, z0);
     return {z0, __dadd_rn(w.z0, w.z1)};
 }
 
@@ -248,8 +254,8 @@ __device__ __forceinline__ double ulp_of(double v) {
 __device__ __forceinline__ uint8_t flag_of(double z0, double z1, const FlagCfg &f) {
     uint8_t r = 0;
     if (!finite_bits(z0) || !finite_bits(z1)) r |= 2;
-    const double az0 = from_bits(bits_of(z0) & 0x7FFFFFFFFFFFFFFFull);   // |z0| by its sign bit
-    const double lim = (f.mode == 0) ? __dmul_rn(f.tau, az0) : __dmul_rn(f.m, ulp_of(z0));
+    // tau >= 0, so |RN(tau z0)| = RN(tau |z0|): the magnitude is taken on the bits
+    const double lim = (f.mode == 0) ? __dmul_rn(f.tau, z0) : __dmul_rn(f.m, ulp_of(z0));
     const uint64_t a = bits_of(z1) & 0x7FFFFFFFFFFFFFFFull, l = bits_of(lim) & 0x7FFFFFFFFFFFFFFFull;
     const uint64_t inf = 0x7FF0000000000000ull;
     if (a <= inf && l <= inf && a > l) r |= 1;

@@ -26,6 +26,7 @@ inline bool params_ok(const tf_params *p) {
     if (!p) return true;
     if (p->panic_mode != TF_PANIC_REL && p->panic_mode != TF_PANIC_ULP) return false;
     if (p->leaf < 1) return false;
+    if (!(p->panic_tau >= 0.0) || !(p->panic_ulps >= 0.0)) return false;   // also rejects NaN
     return true;
 }
 

@@ -108,6 +108,16 @@ TFS_HD float rsqrt_seed(float f) {
 #endif
 }
 
+TFS_HD float u2f(uint32_t u) {
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(u);
+#else
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+
 TFS_HD uint32_t f2u(float f) {
 #if defined(__CUDA_ARCH__)
     return __float_as_uint(f);
@@ -155,6 +165,34 @@ TFS_HD uint64_t float_fixed(float y, int bias) {
     return sh >= 41 ? ~0ull : (m << sh);
 }
 
+// (a 2^32 + b) * m >> k for 0 <= k <= 32, a, b < 2^32, m < 2^24: the high
+// bits of a 64 x 24-bit product from two 32 x 32-bit products.  Sets *ovf
+// when the result does not fit 64 bits.
+TFS_HD uint64_t mul_m24_shr(uint64_t x, uint64_t m, int k, bool *ovf) {
+    const uint64_t A = (x >> 32) * m, B = (x & 0xFFFFFFFFull) * m;   // each < 2^56
+    const uint64_t hi = A << (32 - k), lo = B >> k;
+    *ovf = (A >> (32 + k)) != 0 || hi + lo < hi;
+    return hi + lo;
+}
+
+// Y ~ 2^116 / mb (1/d in 1.63 fixed point, d = mb / 2^53 in [1/2, 1)) from
+// the single-precision seed and ONE Newton step, both products taken with
+// the 24-bit seed significand m: Y never exceeds the true value by more
+// than 2^-61 relative and is below it by at most 2^-43.  (Newton's step
+// from below-by-eps lands below-by-eps^2; eps <= 2^-22 for the seed.)
+TFS_HD uint64_t recip1(uint64_t mb) {
+    const uint32_t v = (uint32_t)(mb >> 29);                   // [2^23, 2^24)
+    const uint32_t ru = f2u(rcp_seed(u2f(0x4B000000u | (v & 0x7FFFFFu))));
+    uint64_t m = (uint64_t)((ru & 0x7FFFFFu) | 0x800000u);
+    int sh = (int)((ru >> 23) & 0xFFu) - 63;                   // y0 = m << sh, sh = 40 or 41
+    if (sh >= 41) { m = 0xFFFFFFull; sh = 40; }                // w at 2: 2^64 - 2^40
+    bool ovf;
+    const uint64_t t = mul_m24_shr(mb << 11, m, 64 - sh, &ovf);   // d w0 2^63
+    const uint64_t e = 0 - t;                                      // (2 - d w0) 2^63
+    const uint64_t y = mul_m24_shr(e, m, 63 - sh, &ovf);           // w0 (2 - d w0) 2^63
+    return ovf ? ~0ull : y;
+}
+
 // Y ~ 2^116 / mb for a 53-bit significand mb in [2^52, 2^53), i.e. 1/d in
 // 1.63 fixed point with d = mb / 2^53 in [1/2, 1); relative error < 2^-60.
 TFS_HD uint64_t recip_fixed(uint64_t mb) {
@@ -175,7 +213,7 @@ TFS_HD uint64_t recip_fixed(uint64_t mb) {
 TFS_HD uint64_t signif(double b) { return (d2u(b) & kFrac) | kHid; }
 
 // Reciprocal of b's significand for div_rn_y; any normal b.
-TFS_HD uint64_t recip_of(double b) { return recip_fixed(signif(b)); }
+TFS_HD uint64_t recip_of(double b) { return recip1(signif(b)); }
 
 // Correctly rounded a / b given y, an estimate of 2^116 / signif(b) with
 // relative error below 2^-52 (recip_of(b), or the reciprocal square root of
@@ -208,18 +246,24 @@ TFS_HD double div_rn_y(double a, double b, uint64_t y_in) {
     const uint64_t ma = (ua & kFrac) | kHid, mb = (ub & kFrac) | kHid;
     const int sh = ma < mb;                              // quotient of significands < 1
     uint64_t y = y_in;
-    if (!y) y = recip_fixed(mb);
-    // q ~ floor(ma 2^(52+sh) / mb) = ma w 2^(sh-1), from (ma 2^11)(w 2^63)/2^64
-    uint64_t q = mulhi(ma << 11, y) >> (11 - sh);
-    // exact remainder of the 2^(52+sh)-scaled quotient, |r| < 2^63
-    int64_t r = (int64_t)((ma << (52 + sh)) - q * mb);
-    if (r < 0) { q -= 1; r += (int64_t)mb; }
-    if (r < 0) { q -= 1; r += (int64_t)mb; }
-    if ((uint64_t)r >= mb) { q += 1; r -= (int64_t)mb; }
-    if ((uint64_t)r >= mb) { q += 1; r -= (int64_t)mb; }
+    if (!y) y = recip1(mb);
+    // Q = floor(ma 2^(52+sh) / mb) = floor(ma w 2^(sh-1)), estimated from
+    // (ma 2^11)(w 2^63)/2^64.  y is at most 2^-52 above 1/d (the reciprocal
+    // root of a rounded square root; recip1 is within 2^-61) and at most
+    // 2^-43 below, so the estimate is at most 3 units above and 2^10 below
+    // Q: q - 4 is below Q and the remainder N - q mb lies in [mb, 2^63.01),
+    // exact modulo 2^64.
+    uint64_t q = (mulhi(ma << 11, y) >> (11 - sh)) - 4;
+    uint64_t r = (ma << (52 + sh)) - q * mb;
+    // one correction step dq ~ r / mb = r y / 2^116, off by at most one
+    const uint64_t dq = mulhi(r, y) >> 52;
+    q += dq;
+    r -= dq * mb;
+    if ((int64_t)r < 0) { q -= 1; r += mb; }
+    if (r >= mb) { q += 1; r -= mb; }
     // round to nearest, ties to even (2r == mb cannot occur for binary64
     // significands, but the rule is kept complete)
-    const uint64_t r2 = (uint64_t)r << 1;
+    const uint64_t r2 = r << 1;
     q += (r2 > mb) | ((r2 == mb) & (q & 1));
     const uint64_t sign = (ua ^ ub) & kSign;
     return u2d(sign | (((uint64_t)(ed + 1022 - sh) << 52) + q));
@@ -384,6 +428,43 @@ TFS_HD double add_rn(double a, double b) {
     return u2d(sign | (r >= inf ? inf : r));
 }
 
+// sqrt(u) correctly rounded, given yx = the reciprocal root that
+// sqrt_rn_y(x) returned for a nearby x (RTF1 takes the root of x0 and of
+// u0 = RN(x0 + x1), usually a few ulps apart).  When u and x share the
+// binade and their significands differ by at most 2^8 units, yx is within
+// 2^-44 of u's reciprocal root: the root estimate is within 2^9 units, one
+// remainder-driven step brings it within two units, and the exact integer
+// remainder finishes as in sqrt_rn_y.  Otherwise the full routine runs.
+TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx) {
+    const uint64_t uu = d2u(u), ux = d2u(x);
+    const int f = (int)(uu >> 52);
+    const uint64_t mu = (uu & kFrac) | kHid, mx = (ux & kFrac) | kHid;
+    const uint64_t diff = mu > mx ? mu - mx : mx - mu;
+    if (yx == 0 || f != (int)(ux >> 52) || (unsigned)(f - 1) >= 2046u || diff > 256) {
+        uint64_t y;
+        return sqrt_rn_y(u, &y);
+    }
+    const int odd = f & 1;
+    const int s = odd ? 52 : 53;
+    const uint64_t m_hi = mu >> (64 - s), m_lo = mu << s;
+    const uint64_t mt = (m_hi << 22) | (m_lo >> 42);
+    // the estimate is within 257 units of Q; 260 below it, the remainder
+    // M - q^2 lies in [0, 2^63.02) and is exact modulo 2^64
+    uint64_t q = (mulhi(mt, yx) >> 10) - 260;
+    uint64_t r = m_lo - q * q;
+    // dq ~ r / (2 q) = r w / 2^54 / ... = mulhi(r, yx) / 2^53
+    const uint64_t dq = mulhi(r, yx) >> 53;
+    q += dq;
+    int64_t rr = (int64_t)(m_lo - q * q);                 // |M - q^2| < 2^60 now
+    if (rr < 0) { q -= 1; rr += (int64_t)(2 * q + 1); }
+    if (rr < 0) { q -= 1; rr += (int64_t)(2 * q + 1); }
+    if (rr > (int64_t)(2 * q)) { rr -= (int64_t)(2 * q + 1); q += 1; }
+    if (rr > (int64_t)(2 * q)) { rr -= (int64_t)(2 * q + 1); q += 1; }
+    q += (uint64_t)(rr > (int64_t)q);
+    const int fr = (f + 1022 + odd) >> 1;
+    return u2d(((uint64_t)(fr - 1) << 52) + q);
+}
+
 // Signed integer significand m and scale q of a finite x = m 2^q.
 TFS_HD void unpack(uint64_t u, int64_t &m, int &q) {
     const int e = (int)((u >> 52) & 0x7FF);
@@ -420,13 +501,18 @@ TFS_HD double literal_sum_err(double a, double b, double s) {
 // is formed modulo 2^64 when the exponent gap is at most 60.  With a larger
 // gap the smaller operand is below a quarter ulp of the larger: s is the
 // larger operand and t the smaller one.
-TFS_HD double sum_err(double a, double b, double s) {
-    const uint64_t ua = d2u(a), ub = d2u(b), us = d2u(s);
+TFS_HD uint64_t sum_err_bits(uint64_t ua, uint64_t ub, uint64_t us);
+
+TFS_HD double sum_err(double a, double b, double s) { return u2d(sum_err_bits(d2u(a), d2u(b), d2u(s))); }
+
+// The same on bit patterns (so that a caller can negate an operand by its
+// sign bit without the compiler forming a floating-point negation).
+TFS_HD uint64_t sum_err_bits(uint64_t ua, uint64_t ub, uint64_t us) {
     const unsigned fa = (unsigned)((ua >> 52) & 0x7FF), fb = (unsigned)((ub >> 52) & 0x7FF);
     if ((fa >= 2045) | (fb >= 2045)) {
         // an Inf or NaN operand makes every variant of the literal sequence NaN
-        if ((fa == 0x7FF) | (fb == 0x7FF)) return u2d(0x7FF8000000000000ull);
-        return literal_sum_err(a, b, s);
+        if ((fa == 0x7FF) | (fb == 0x7FF)) return 0x7FF8000000000000ull;
+        return d2u(literal_sum_err(u2d(ua), u2d(ub), u2d(us)));
     }
     int64_t ma, mb, ms;
     int qa, qb, qs;
@@ -438,23 +524,23 @@ TFS_HD double sum_err(double a, double b, double s) {
     if (gap > 60) {
         // t = the operand with the finer ulp (never -0: a zero error is +0)
         const uint64_t small = qa < qb ? ua : ub;
-        return u2d((small << 1) ? small : 0);
+        return (small << 1) ? small : 0;
     }
     int64_t big = (int64_t)(shl_mod(ma, qa - qmin) + shl_mod(mb, qb - qmin));
     // s is a multiple of 2^qmin; its own scale may be finer when the sum cancels
     const int ds = qs - qmin;
     int64_t sv = ds >= 0 ? (int64_t)shl_mod(ms, ds) : (ms >> (-ds));
     const int64_t t = big - sv;
-    if (t == 0) return 0.0;
+    if (t == 0) return 0;
     const uint64_t sign = t < 0 ? kSign : 0;
     const uint64_t mag = (uint64_t)(t < 0 ? -t : t);
     const int lz = clz64(mag);
     const int lead = 63 - lz + qmin;                     // exponent of the leading bit
     if (lead >= -1022) {
         const uint64_t frac = ((mag << lz) >> 11) & kFrac;   // exact: t fits 53 bits
-        return u2d(sign | ((uint64_t)(lead + 1023) << 52) | frac);
+        return sign | ((uint64_t)(lead + 1023) << 52) | frac;
     }
-    return u2d(sign | (mag << (qmin + 1074)));          // subnormal tail
+    return sign | (mag << (qmin + 1074));               // subnormal tail
 }
 
 }  // namespace soft

@@ -231,6 +231,28 @@ int64_t check_add(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
     return nbad;
 }
 
+// sqrt(u) from the reciprocal root of sqrt(x) for u within a few hundred
+// ulps of x (RTF1's second root), including binade crossings and far
+// values that take the full path.
+int64_t check_sqrt_near(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double x = std::fabs(rnd(key, i, 1, 2046));
+        int64_t k = (int64_t)(mix(key ^ (uint64_t)i) % 1200) - 600;   // ulps, some beyond 256
+        if (i % 11 == 0) x = u2d((d2u(x) & ~kFrac) | (i & 1 ? 0 : kFrac));   // binade edges
+        double u = u2d(d2u(x) + k);
+        if (!(u > 0) || std::isinf(u)) continue;
+        uint64_t yx;
+        (void)sqrt_rn_y(x, &yx);
+        volatile double ref = std::sqrt(u);
+        if (!same(sqrt_rn_near(u, x, yx), ref)) {
+            if (!nbad) { bad[0] = u; bad[1] = x; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 // Perfect squares and their neighbours.
 int64_t check_sqrt_hard(uint64_t key, int64_t n, double *bad) {
     int64_t nbad = 0;

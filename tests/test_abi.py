@@ -94,6 +94,10 @@ def test_reduce_rejects_bad_offsets_and_small_workspace(L):
     assert L.twofold_dot_batched(x, x, offs.ctypes.data, 40, out, None, FAKE, 16, None) == T.TF_ENOSPC
     bad = T.params(leaf=0)
     assert L.twofold_dot(x, x, 100, out, ctypes.byref(bad), FAKE, 1 << 20, None) == T.TF_EINVAL
+    bad = T.params(panic_tau=-1.0)
+    assert L.twofold_dot(x, x, 100, out, ctypes.byref(bad), FAKE, 1 << 20, None) == T.TF_EINVAL
+    bad = T.params(panic_ulps=float("nan"))
+    assert L.twofold_dot(x, x, 100, out, ctypes.byref(bad), FAKE, 1 << 20, None) == T.TF_EINVAL
     bad = T.params(panic_mode=7)
     assert L.twofold_sum(x, 100, out, ctypes.byref(bad), FAKE, 1 << 20, None) == T.TF_EINVAL
     assert L.twofold_sum(x, -5, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL

@@ -23,7 +23,8 @@ def H(tmp_path_factory):
                  "check_add"):
         getattr(L, name).argtypes = [u64, i64, ctypes.c_int, ctypes.c_int, p]
         getattr(L, name).restype = i64
-    for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared"):
+    for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared",
+                 "check_sqrt_near"):
         getattr(L, name).argtypes = [u64, i64, p]
         getattr(L, name).restype = i64
     L.soft_div.argtypes = [d, d]
@@ -88,6 +89,7 @@ def test_div_with_reused_reciprocals(H, scale):
     try:
         run(H, "check_div_by_root", 19, 2_000_000)
         run(H, "check_div_shared", 20, 2_000_000)
+        run(H, "check_sqrt_near", 29, 2_000_000)
     finally:
         H.set_seed_scale(1.0)
 
