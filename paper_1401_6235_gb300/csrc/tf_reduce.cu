@@ -35,6 +35,8 @@ struct RedArgs {
     int njobs;
     int64_t L;
     int B;                     // leaves per block (power of two, <= kThreads)
+    int C;                     // elements of each leaf staged per chunk (power of two)
+    int narr;                  // staged arrays: x, [x tails], [y, [y tails]]
     Tab tab;
     double *part0, *part1;     // partial results, one per block
     double *out_hi, *out_lo;
@@ -52,23 +54,60 @@ __device__ __forceinline__ int job_of(const Tab &T, int njobs, int64_t b) {
     return lo;
 }
 
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// One element of a leaf: acc = ATF1(acc, term) (ATF1.1 for a dotted sum).
 template <bool DOT, bool PLAIN>
-__device__ __forceinline__ tf::d2 leaf(const RedArgs &A, int64_t b, int64_t e) {
-    tf::d2 acc = {0.0, 0.0};
-    const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
-    for (int64_t i = b; i < e; ++i) {
-        if (PLAIN) {
-            double term = DOT ? __dmul_rn(A.xh[i], A.yh[i]) : A.xh[i];
-            acc.z0 = __dadd_rn(acc.z0, term);
-        } else if (!DOT) {
-            acc = xd ? tf::atf11(acc.z0, acc.z1, A.xh[i]) : tf::atf1(acc.z0, acc.z1, A.xh[i], A.xl[i]);
+__device__ __forceinline__ void leaf_step(tf::d2 &acc, double x0, double x1, bool xd, double y0, double y1,
+                                          bool yd) {
+    if (PLAIN) {
+        acc.z0 = __dadd_rn(acc.z0, DOT ? __dmul_rn(x0, y0) : x0);
+    } else if (!DOT) {
+        acc = xd ? tf::atf11(acc.z0, acc.z1, x0) : tf::atf1(acc.z0, acc.z1, x0, x1);
+    } else {
+        const tf::d2 p = tf::apply(tf::OP_MUL, x0, x1, xd, y0, y1, yd);
+        acc = tf::atf1(acc.z0, acc.z1, p.z0, p.z1);
+    }
+}
+
+// Eight consecutive elements of a leaf with the same operations as
+// leaf_step, scheduled for latency: the terms first, then the z0 chain
+// (acc0 + term0, eight dependent additions), then the eight Two-Sum tails
+// (independent of one another; the literal sequence, native), then the z1
+// chain.  Every value is the one leaf_step computes.
+template <bool DOT>
+__device__ __forceinline__ void leaf_step8(tf::d2 &acc, const double *X, const double *XL, const double *Y,
+                                           const double *YL) {
+    double p[8], e[8], a0[8], s[8], t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        if (DOT) {
+            const tf::d2 q = tf::apply(tf::OP_MUL, X[u], XL ? XL[u] : 0.0, XL == nullptr, Y[u],
+                                       YL ? YL[u] : 0.0, YL == nullptr);
+            p[u] = q.z0;
+            e[u] = q.z1;
         } else {
-            tf::d2 p = tf::apply(tf::OP_MUL, A.xh[i], xd ? 0.0 : A.xl[i], xd, A.yh[i],
-                                 yd ? 0.0 : A.yl[i], yd);
-            acc = tf::atf1(acc.z0, acc.z1, p.z0, p.z1);
+            p[u] = X[u];
+            e[u] = XL ? XL[u] : 0.0;
         }
     }
-    return acc;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        a0[u] = acc.z0;
+        s[u] = __dadd_rn(acc.z0, p[u]);
+        acc.z0 = s[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = tf::soft::literal_sum_err(a0[u], p[u], s[u]);
+    const bool has_e = DOT || XL != nullptr;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc.z1 = has_e ? __dadd_rn(__dadd_rn(acc.z1, e[u]), t[u]) : __dadd_rn(acc.z1, t[u]);
 }
 
 template <bool PLAIN>
@@ -86,8 +125,14 @@ __device__ __forceinline__ void write_result(const RedArgs &A, int j, tf::d2 r) 
     }
 }
 
-template <bool DOT, bool PLAIN>
+// One CTA reduces an aligned block of B leaves.  The leaves' elements are
+// staged chunk by chunk (C elements per leaf) into shared memory with
+// cp.async, double buffered, rows padded to C+1 words; thread t then walks
+// leaf t's row in order.  LAT: few leaves per CTA (latency-bound jobs), the
+// eight-element latency schedule.
+template <bool DOT, bool PLAIN, bool LAT>
 __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant__ RedArgs A) {
+    extern __shared__ double stage[];                // [2][narr][B][C+1]
     __shared__ double s0[kThreads], s1[kThreads];
     const int t = threadIdx.x;
     const int64_t b = blockIdx.x;
@@ -96,12 +141,65 @@ __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant_
     const int64_t m = (len + A.L - 1) / A.L;
     const int64_t leaf0 = (b - A.tab.b0(j)) * A.B;
     const int nl = (int)min((int64_t)A.B, m - leaf0);
+    const int B = A.B, C = A.C, S = C + 1, narr = A.narr;
+    const int64_t base = e0 + leaf0 * A.L;           // first element of the block
+    const int64_t end = e0 + len;
+    const double *src[4] = {nullptr, nullptr, nullptr, nullptr};
+    int na = 0;
+    src[na++] = A.xh;
+    if (A.xl) src[na++] = A.xl;
+    if (DOT) {
+        src[na++] = A.yh;
+        if (A.yl) src[na++] = A.yl;
+    }
+    const int lgC = __ffs(C) - 1;
+    const int64_t nch = (A.L + C - 1) / C;           // chunks per (full) leaf
+
+    auto load = [&](int64_t c, int buf) {
+        double *dst = stage + (size_t)buf * narr * B * S;
+        for (int idx = t; idx < nl * C; idx += kThreads) {
+            const int row = idx >> lgC, k = idx & (C - 1);
+            const int64_t off = c * C + k;
+            const int64_t g = base + (int64_t)row * A.L + off;
+            if (off < A.L && g < end) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    if (a < na) cp_async8(dst + ((size_t)a * B + row) * S + k, src[a] + g);
+            }
+        }
+        cp_commit();
+    };
+
+    tf::d2 acc = {0.0, 0.0};
+    const int64_t lb = base + (int64_t)t * A.L;      // this thread's leaf
+    const int64_t llen = t < nl ? min(A.L, end - lb) : 0;
+    const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
+    load(0, 0);
+    for (int64_t c = 0; c < nch; ++c) {
+        if (c + 1 < nch) { load(c + 1, (int)((c + 1) & 1)); cp_wait_one(); }
+        else cp_wait_all();
+        __syncthreads();
+        const double *buf = stage + (size_t)(c & 1) * narr * B * S;
+        const int cnt = (int)max((int64_t)0, min((int64_t)C, llen - c * C));
+        if (cnt > 0) {
+            int a = 0;
+            const double *X = buf + ((size_t)(a++) * B + t) * S;
+            const double *XL = xd ? nullptr : buf + ((size_t)(a++) * B + t) * S;
+            const double *Y = DOT ? buf + ((size_t)(a++) * B + t) * S : nullptr;
+            const double *YL = (DOT && !yd) ? buf + ((size_t)(a++) * B + t) * S : nullptr;
+            int k = 0;
+            if (LAT && !PLAIN)
+                for (; k + 8 <= cnt; k += 8)
+                    leaf_step8<DOT>(acc, X + k, XL ? XL + k : nullptr, DOT ? Y + k : nullptr, YL ? YL + k : nullptr);
+            for (; k < cnt; ++k)
+                leaf_step<DOT, PLAIN>(acc, X[k], xd ? 0.0 : XL[k], xd, DOT ? Y[k] : 0.0,
+                                      (DOT && !yd) ? YL[k] : 0.0, yd);
+        }
+        __syncthreads();
+    }
     if (t < nl) {
-        const int64_t lb = e0 + (leaf0 + t) * A.L;
-        const int64_t le = min(lb + A.L, e0 + len);
-        tf::d2 r = leaf<DOT, PLAIN>(A, lb, le);
-        s0[t] = r.z0;
-        s1[t] = r.z1;
+        s0[t] = acc.z0;
+        s1[t] = acc.z1;
     }
     __syncthreads();
     for (int s = 1; s < nl; s <<= 1) {
@@ -164,6 +262,18 @@ int leaves_per_block(int64_t M) {
     int B = 1;
     while (B < kThreads && (int64_t)B * 2 * 1024 <= M) B <<= 1;
     return B;
+}
+
+// Elements of each leaf staged per chunk: a power of two with both buffers
+// of all staged arrays within ~96 KiB of shared memory, and no larger than
+// the leaf rounded up to a power of two.
+int chunk_of(int B, int narr, int64_t L) {
+    const int64_t budget = 6144 / ((int64_t)narr * B);     // elements per row and buffer
+    int C = 1;
+    while ((int64_t)C * 2 <= budget) C <<= 1;
+    int64_t lp = 1;
+    while (lp < L) lp <<= 1;
+    return (int)(C < lp ? C : lp);
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -236,7 +346,18 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
         A.part0 = reinterpret_cast<double *>(w);
         A.part1 = reinterpret_cast<double *>(w + align256(sizeof(double) * (size_t)nblk));
     }
-    if (nblk > 0) reduce_blocks<DOT, PLAIN><<<(unsigned)nblk, kThreads, 0, s>>>(A);
+    A.narr = 1 + (xl != nullptr) + (DOT ? 1 + (yl != nullptr) : 0);
+    A.C = chunk_of(B, A.narr, L);
+    if (nblk > 0) {
+        const size_t smem = (size_t)2 * A.narr * B * (A.C + 1) * sizeof(double);
+        const bool lat = B < 32;
+        const void *k = lat ? (const void *)reduce_blocks<DOT, PLAIN, true> : (const void *)reduce_blocks<DOT, PLAIN, false>;
+        if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                                    cudaSuccess)
+            return TF_ECUDA;
+        if (lat) reduce_blocks<DOT, PLAIN, true><<<(unsigned)nblk, kThreads, smem, s>>>(A);
+        else reduce_blocks<DOT, PLAIN, false><<<(unsigned)nblk, kThreads, smem, s>>>(A);
+    }
     if (need_final) reduce_final<PLAIN><<<njobs, kThreads, 0, s>>>(A);
     return tfh::launch_status();
 }
