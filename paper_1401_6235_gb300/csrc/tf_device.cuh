@@ -236,6 +236,7 @@ struct FlagCfg {
     int mode;      // 0 REL, 1 ULP
     double tau;    // REL threshold
     double m;      // ULP threshold
+    int k;         // REL: tau = 2^k exactly (k <= 0), else 1 (use the multiplication)
 };
 
 // ulp(v) = 2^(max(e,-1022)-52) from the exponent field; NaN for Inf/NaN.
@@ -254,9 +255,16 @@ __device__ __forceinline__ double ulp_of(double v) {
 __device__ __forceinline__ uint8_t flag_of(double z0, double z1, const FlagCfg &f) {
     uint8_t r = 0;
     if (!finite_bits(z0) || !finite_bits(z1)) r |= 2;
-    // tau >= 0, so |RN(tau z0)| = RN(tau |z0|): the magnitude is taken on the bits
-    const double lim = (f.mode == 0) ? __dmul_rn(f.tau, z0) : __dmul_rn(f.m, ulp_of(z0));
-    const uint64_t a = bits_of(z1) & 0x7FFFFFFFFFFFFFFFull, l = bits_of(lim) & 0x7FFFFFFFFFFFFFFFull;
+    // tau >= 0, so |RN(tau z0)| = RN(tau |z0|): the magnitude is taken on the
+    // bits; a power-of-two tau (the default 2^-40) scales in integer form
+    uint64_t l;
+    if (f.mode == 0) {
+        if (f.k <= 0) l = soft::scale_abs_pow2(bits_of(z0), f.k);
+        else l = bits_of(__dmul_rn(f.tau, z0)) & 0x7FFFFFFFFFFFFFFFull;
+    } else {
+        l = bits_of(__dmul_rn(f.m, ulp_of(z0))) & 0x7FFFFFFFFFFFFFFFull;
+    }
+    const uint64_t a = bits_of(z1) & 0x7FFFFFFFFFFFFFFFull;
     const uint64_t inf = 0x7FF0000000000000ull;
     if (a <= inf && l <= inf && a > l) r |= 1;
     return r;

@@ -2,6 +2,7 @@
 // defaults, argument checks, launch-error mapping.
 #pragma once
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstdint>
 #include <cstddef>
 
@@ -19,6 +20,10 @@ inline tf::FlagCfg flag_cfg(const tf_params *p) {
     f.mode = p ? p->panic_mode : TF_PANIC_REL;
     f.tau = p ? p->panic_tau : kDefaultTau;
     f.m = p ? p->panic_ulps : kDefaultUlps;
+    // tau = 2^k with -1074 <= k <= 0 and a normal power of two: integer scaling
+    f.k = 1;
+    int e = 0;
+    if (f.tau > 0.0 && std::frexp(f.tau, &e) == 0.5 && e - 1 <= 0 && e - 1 >= -1022) f.k = e - 1;
     return f;
 }
 

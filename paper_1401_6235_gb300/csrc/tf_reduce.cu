@@ -20,6 +20,8 @@ namespace {
 
 constexpr int kThreads = 256;        // = maximum leaves per block
 constexpr int kInlineJobs = 32;      // job tables up to this size travel in the launch params
+constexpr int64_t kLatMaxLeaves = 2048;   // latency schedule: at most this many leaves in all
+constexpr int64_t kLatMaxLeaf = 1024;     // ... each at most this long (4 L doubles of shared memory)
 
 struct Tab {
     const int64_t *offs;   // device job table (njobs+1), or nullptr: use the inline copy
@@ -76,40 +78,6 @@ __device__ __forceinline__ void leaf_step(tf::d2 &acc, double x0, double x1, boo
     }
 }
 
-// Eight consecutive elements of a leaf with the same operations as
-// leaf_step, scheduled for latency: the terms first, then the z0 chain
-// (acc0 + term0, eight dependent additions), then the eight Two-Sum tails
-// (independent of one another; the literal sequence, native), then the z1
-// chain.  Every value is the one leaf_step computes.
-template <bool DOT>
-__device__ __forceinline__ void leaf_step8(tf::d2 &acc, const double *X, const double *XL, const double *Y,
-                                           const double *YL) {
-    double p[8], e[8], a0[8], s[8], t[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        if (DOT) {
-            const tf::d2 q = tf::apply(tf::OP_MUL, X[u], XL ? XL[u] : 0.0, XL == nullptr, Y[u],
-                                       YL ? YL[u] : 0.0, YL == nullptr);
-            p[u] = q.z0;
-            e[u] = q.z1;
-        } else {
-            p[u] = X[u];
-            e[u] = XL ? XL[u] : 0.0;
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        a0[u] = acc.z0;
-        s[u] = __dadd_rn(acc.z0, p[u]);
-        acc.z0 = s[u];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) t[u] = tf::soft::literal_sum_err(a0[u], p[u], s[u]);
-    const bool has_e = DOT || XL != nullptr;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc.z1 = has_e ? __dadd_rn(__dadd_rn(acc.z1, e[u]), t[u]) : __dadd_rn(acc.z1, t[u]);
-}
-
 template <bool PLAIN>
 __device__ __forceinline__ tf::d2 combine(tf::d2 l, tf::d2 r) {
     if (PLAIN) return {__dadd_rn(l.z0, r.z0), 0.0};
@@ -125,14 +93,16 @@ __device__ __forceinline__ void write_result(const RedArgs &A, int j, tf::d2 r) 
     }
 }
 
-// One CTA reduces an aligned block of B leaves.  The leaves' elements are
-// staged chunk by chunk (C elements per leaf) into shared memory with
-// cp.async, double buffered, rows padded to C+1 words; thread t then walks
-// leaf t's row in order.  LAT: few leaves per CTA (latency-bound jobs), the
-// eight-element latency schedule.
-template <bool DOT, bool PLAIN, bool LAT>
+// One CTA reduces an aligned block of B leaves, one leaf per thread, then
+// an in-place strided tree in shared memory.  STAGED: the leaves' elements
+// are staged chunk by chunk (C elements per leaf) into shared memory with
+// cp.async, double buffered, rows padded to C+1 words, and thread t walks
+// leaf t's row (used by the memory-bound plain twin); otherwise thread t
+// reads its leaf straight from global memory through L1 (the twofold step
+// is compute-bound and barrier-free this way).
+template <bool DOT, bool PLAIN, bool STAGED>
 __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant__ RedArgs A) {
-    extern __shared__ double stage[];                // [2][narr][B][C+1]
+    extern __shared__ double stage[];                // [2][narr][B][C+1] when STAGED
     __shared__ double s0[kThreads], s1[kThreads];
     const int t = threadIdx.x;
     const int64_t b = blockIdx.x;
@@ -141,61 +111,61 @@ __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant_
     const int64_t m = (len + A.L - 1) / A.L;
     const int64_t leaf0 = (b - A.tab.b0(j)) * A.B;
     const int nl = (int)min((int64_t)A.B, m - leaf0);
-    const int B = A.B, C = A.C, S = C + 1, narr = A.narr;
     const int64_t base = e0 + leaf0 * A.L;           // first element of the block
     const int64_t end = e0 + len;
-    const double *src[4] = {nullptr, nullptr, nullptr, nullptr};
-    int na = 0;
-    src[na++] = A.xh;
-    if (A.xl) src[na++] = A.xl;
-    if (DOT) {
-        src[na++] = A.yh;
-        if (A.yl) src[na++] = A.yl;
-    }
-    const int lgC = __ffs(C) - 1;
-    const int64_t nch = (A.L + C - 1) / C;           // chunks per (full) leaf
-
-    auto load = [&](int64_t c, int buf) {
-        double *dst = stage + (size_t)buf * narr * B * S;
-        for (int idx = t; idx < nl * C; idx += kThreads) {
-            const int row = idx >> lgC, k = idx & (C - 1);
-            const int64_t off = c * C + k;
-            const int64_t g = base + (int64_t)row * A.L + off;
-            if (off < A.L && g < end) {
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-                    if (a < na) cp_async8(dst + ((size_t)a * B + row) * S + k, src[a] + g);
-            }
-        }
-        cp_commit();
-    };
-
-    tf::d2 acc = {0.0, 0.0};
     const int64_t lb = base + (int64_t)t * A.L;      // this thread's leaf
     const int64_t llen = t < nl ? min(A.L, end - lb) : 0;
     const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
-    load(0, 0);
-    for (int64_t c = 0; c < nch; ++c) {
-        if (c + 1 < nch) { load(c + 1, (int)((c + 1) & 1)); cp_wait_one(); }
-        else cp_wait_all();
-        __syncthreads();
-        const double *buf = stage + (size_t)(c & 1) * narr * B * S;
-        const int cnt = (int)max((int64_t)0, min((int64_t)C, llen - c * C));
-        if (cnt > 0) {
-            int a = 0;
-            const double *X = buf + ((size_t)(a++) * B + t) * S;
-            const double *XL = xd ? nullptr : buf + ((size_t)(a++) * B + t) * S;
-            const double *Y = DOT ? buf + ((size_t)(a++) * B + t) * S : nullptr;
-            const double *YL = (DOT && !yd) ? buf + ((size_t)(a++) * B + t) * S : nullptr;
-            int k = 0;
-            if (LAT && !PLAIN)
-                for (; k + 8 <= cnt; k += 8)
-                    leaf_step8<DOT>(acc, X + k, XL ? XL + k : nullptr, DOT ? Y + k : nullptr, YL ? YL + k : nullptr);
-            for (; k < cnt; ++k)
-                leaf_step<DOT, PLAIN>(acc, X[k], xd ? 0.0 : XL[k], xd, DOT ? Y[k] : 0.0,
-                                      (DOT && !yd) ? YL[k] : 0.0, yd);
+    tf::d2 acc = {0.0, 0.0};
+    if (!STAGED) {
+        for (int64_t i = lb; i < lb + llen; ++i)
+            leaf_step<DOT, PLAIN>(acc, A.xh[i], xd ? 0.0 : A.xl[i], xd, DOT ? A.yh[i] : 0.0,
+                                  (DOT && !yd) ? A.yl[i] : 0.0, yd);
+    } else {
+        const int B = A.B, C = A.C, S = C + 1, narr = A.narr;
+        const double *src[4] = {nullptr, nullptr, nullptr, nullptr};
+        int na = 0;
+        src[na++] = A.xh;
+        if (A.xl) src[na++] = A.xl;
+        if (DOT) {
+            src[na++] = A.yh;
+            if (A.yl) src[na++] = A.yl;
         }
-        __syncthreads();
+        const int lgC = __ffs(C) - 1;
+        const int64_t nch = (A.L + C - 1) / C;       // chunks per (full) leaf
+        auto load = [&](int64_t c, int buf) {
+            double *dst = stage + (size_t)buf * narr * B * S;
+            for (int idx = t; idx < nl * C; idx += kThreads) {
+                const int row = idx >> lgC, k = idx & (C - 1);
+                const int64_t off = c * C + k;
+                const int64_t g = base + (int64_t)row * A.L + off;
+                if (off < A.L && g < end) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        if (a < na) cp_async8(dst + ((size_t)a * B + row) * S + k, src[a] + g);
+                }
+            }
+            cp_commit();
+        };
+        load(0, 0);
+        for (int64_t c = 0; c < nch; ++c) {
+            if (c + 1 < nch) { load(c + 1, (int)((c + 1) & 1)); cp_wait_one(); }
+            else cp_wait_all();
+            __syncthreads();
+            const double *buf = stage + (size_t)(c & 1) * narr * B * S;
+            const int cnt = (int)max((int64_t)0, min((int64_t)C, llen - c * C));
+            if (cnt > 0) {
+                int a = 0;
+                const double *X = buf + ((size_t)(a++) * B + t) * S;
+                const double *XL = xd ? nullptr : buf + ((size_t)(a++) * B + t) * S;
+                const double *Y = DOT ? buf + ((size_t)(a++) * B + t) * S : nullptr;
+                const double *YL = (DOT && !yd) ? buf + ((size_t)(a++) * B + t) * S : nullptr;
+                for (int k = 0; k < cnt; ++k)
+                    leaf_step<DOT, PLAIN>(acc, X[k], xd ? 0.0 : XL[k], xd, DOT ? Y[k] : 0.0,
+                                          (DOT && !yd) ? YL[k] : 0.0, yd);
+            }
+            __syncthreads();
+        }
     }
     if (t < nl) {
         s0[t] = acc.z0;
@@ -212,6 +182,71 @@ __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant_
     }
     if (t == 0) {
         const tf::d2 r = {s0[0], s1[0]};
+        if (A.tab.b0(j + 1) - A.tab.b0(j) == 1) write_result<PLAIN>(A, j, r);
+        else { A.part0[b] = r.z0; A.part1[b] = r.z1; }
+    }
+}
+
+// Latency schedule for jobs with few leaves: one CTA per leaf (B = 1).
+// The leaf's left-to-right accumulation acc = ATF1(acc, term_i) is split
+// into its independent and its sequential parts, in this order:
+//   terms (p_i, e_i) of all elements        - all threads, in parallel
+//   z0 chain  a_i = acc0, acc0 = acc0 + p_i  - one thread (one FP64 add per step)
+//   tails     t_i = Two-Sum tail(a_i, p_i)   - all threads, in parallel
+//   z1 chain  acc1 = (acc1 + e_i) + t_i      - one thread (acc1 + t_i for ATF1.1)
+// Every operation and operand is the one the sequential leaf uses, so the
+// bits are the same; a lane-serial FP64 chain costs a full warp slot per
+// operation on this GPU, so only the two chains stay serial.
+template <bool DOT, bool PLAIN>
+__global__ void __launch_bounds__(kThreads) reduce_lat(const __grid_constant__ RedArgs A) {
+    extern __shared__ double lat[];                  // P, E, A0, S (also T) : 4 x L
+    const int t = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    const int j = job_of(A.tab, A.njobs, b);
+    const int64_t e0 = A.tab.off(j), len = A.tab.off(j + 1) - e0;
+    const int64_t leaf = b - A.tab.b0(j);
+    const int64_t lb = e0 + leaf * A.L;
+    const int llen = (int)min(A.L, e0 + len - lb);
+    const int L = (int)A.L;
+    double *P = lat, *E = lat + L, *A0 = lat + 2 * L, *S = lat + 3 * L;
+    const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
+    for (int i = t; i < llen; i += kThreads) {
+        const int64_t g = lb + i;
+        if (PLAIN) {
+            P[i] = DOT ? __dmul_rn(A.xh[g], A.yh[g]) : A.xh[g];
+        } else if (DOT) {
+            const tf::d2 q = tf::apply(tf::OP_MUL, A.xh[g], xd ? 0.0 : A.xl[g], xd, A.yh[g],
+                                       yd ? 0.0 : A.yl[g], yd);
+            P[i] = q.z0;
+            E[i] = q.z1;
+        } else {
+            P[i] = A.xh[g];
+            if (!xd) E[i] = A.xl[g];
+        }
+    }
+    __syncthreads();
+    double acc0 = 0.0, acc1 = 0.0;
+    if (t == 0) {
+#pragma unroll 8
+        for (int i = 0; i < llen; ++i) {
+            if (!PLAIN) A0[i] = acc0;
+            acc0 = __dadd_rn(acc0, P[i]);
+            if (!PLAIN) S[i] = acc0;
+        }
+    }
+    if (!PLAIN) {
+        __syncthreads();
+        for (int i = t; i < llen; i += kThreads) S[i] = tf::soft::sum_err(A0[i], P[i], S[i]);   // S now holds t_i
+        __syncthreads();
+        const bool has_e = DOT || !xd;
+        if (t == 0) {
+#pragma unroll 8
+            for (int i = 0; i < llen; ++i)
+                acc1 = has_e ? __dadd_rn(__dadd_rn(acc1, E[i]), S[i]) : __dadd_rn(acc1, S[i]);
+        }
+    }
+    if (t == 0) {
+        const tf::d2 r = {acc0, acc1};
         if (A.tab.b0(j + 1) - A.tab.b0(j) == 1) write_result<PLAIN>(A, j, r);
         else { A.part0[b] = r.z0; A.part1[b] = r.z1; }
     }
@@ -302,7 +337,9 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
     std::vector<int64_t> tab(2 * (size_t)(njobs + 1));
     int64_t M = 0;
     for (int j = 0; j < njobs; ++j) M += (offs[j + 1] - offs[j] + L - 1) / L;
-    const int B = leaves_per_block(M);
+    // few leaves of moderate length: the latency schedule, one CTA per leaf
+    const bool lat = M <= kLatMaxLeaves && L <= kLatMaxLeaf;
+    const int B = lat ? 1 : leaves_per_block(M);
     int64_t nblk = 0;
     bool need_final = false;
     for (int j = 0; j < njobs; ++j) {
@@ -349,14 +386,23 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
     A.narr = 1 + (xl != nullptr) + (DOT ? 1 + (yl != nullptr) : 0);
     A.C = chunk_of(B, A.narr, L);
     if (nblk > 0) {
-        const size_t smem = (size_t)2 * A.narr * B * (A.C + 1) * sizeof(double);
-        const bool lat = B < 32;
-        const void *k = lat ? (const void *)reduce_blocks<DOT, PLAIN, true> : (const void *)reduce_blocks<DOT, PLAIN, false>;
-        if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                                    cudaSuccess)
-            return TF_ECUDA;
-        if (lat) reduce_blocks<DOT, PLAIN, true><<<(unsigned)nblk, kThreads, smem, s>>>(A);
-        else reduce_blocks<DOT, PLAIN, false><<<(unsigned)nblk, kThreads, smem, s>>>(A);
+        if (lat) {
+            const size_t smem = (size_t)4 * L * sizeof(double);
+            if (smem > 48 * 1024 && cudaFuncSetAttribute(reduce_lat<DOT, PLAIN>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)smem) != cudaSuccess)
+                return TF_ECUDA;
+            reduce_lat<DOT, PLAIN><<<(unsigned)nblk, kThreads, smem, s>>>(A);
+        } else if (PLAIN) {
+            const size_t smem = (size_t)2 * A.narr * B * (A.C + 1) * sizeof(double);
+            if (smem > 48 * 1024 && cudaFuncSetAttribute(reduce_blocks<DOT, PLAIN, true>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)smem) != cudaSuccess)
+                return TF_ECUDA;
+            reduce_blocks<DOT, PLAIN, true><<<(unsigned)nblk, kThreads, smem, s>>>(A);
+        } else {
+            reduce_blocks<DOT, PLAIN, false><<<(unsigned)nblk, kThreads, 0, s>>>(A);
+        }
     }
     if (need_final) reduce_final<PLAIN><<<njobs, kThreads, 0, s>>>(A);
     return tfh::launch_status();

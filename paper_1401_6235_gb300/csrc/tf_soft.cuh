@@ -128,9 +128,14 @@ TFS_HD uint32_t f2u(float f) {
 #endif
 }
 
+// The native fallbacks are volatile inline PTX on the device, so that the
+// compiler never evaluates them speculatively on lanes that do not take the
+// fallback branch (a native division or root is ~8 FP64 issue slots).
 TFS_HD double native_div(double a, double b) {
 #if defined(__CUDA_ARCH__)
-    return __ddiv_rn(a, b);
+    double r;
+    asm volatile("div.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
 #else
     volatile double r = a / b;
     return r;
@@ -139,7 +144,9 @@ TFS_HD double native_div(double a, double b) {
 
 TFS_HD double native_sqrt(double a) {
 #if defined(__CUDA_ARCH__)
-    return __dsqrt_rn(a);
+    double r;
+    asm volatile("sqrt.rn.f64 %0, %1;" : "=d"(r) : "d"(a));
+    return r;
 #else
     volatile double r = std::sqrt(a);
     return r;
@@ -148,7 +155,9 @@ TFS_HD double native_sqrt(double a) {
 
 TFS_HD double native_add(double a, double b) {
 #if defined(__CUDA_ARCH__)
-    return __dadd_rn(a, b);
+    double r;
+    asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
 #else
     volatile double r = a + b;
     return r;
@@ -336,7 +345,9 @@ TFS_HD double twice(double c) {
 
 TFS_HD double native_mul(double a, double b) {
 #if defined(__CUDA_ARCH__)
-    return __dmul_rn(a, b);
+    double r;
+    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
 #else
     volatile double r = a * b;
     return r;
@@ -465,6 +476,22 @@ TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx) {
     return u2d(((uint64_t)(fr - 1) << 52) + q);
 }
 
+// RN(|z| 2^k) as bits for an integer k <= 0 (the scaling of a panic
+// threshold that is a power of two), exact for results in the normal range,
+// round to nearest even into the subnormal range, Inf and NaN kept.
+TFS_HD uint64_t scale_abs_pow2(uint64_t uz, int k) {
+    const uint64_t a = uz & ~kSign;
+    const int f = (int)(a >> 52);
+    if (f == 0x7FF || a == 0) return a;
+    if (f + k >= 1) return a + ((uint64_t)(int64_t)k << 52);   // stays normal: exponent shift
+    // subnormal result: significand (with hidden bit when normal) >> (1 - f - k), or >> -k
+    const uint64_t m = f ? ((a & kFrac) | kHid) : a;
+    const int sh = f ? (1 - f - k) : -k;
+    if (sh >= 64) return 0;
+    const uint64_t q = m >> sh, rem = m & ((1ull << sh) - 1), half = sh ? (1ull << (sh - 1)) : 0;
+    return q + ((rem > half) | ((rem == half) & (q & 1) & (sh > 0)));
+}
+
 // Signed integer significand m and scale q of a finite x = m 2^q.
 TFS_HD void unpack(uint64_t u, int64_t &m, int &q) {
     const int e = (int)((u >> 52) & 0x7FF);
@@ -479,8 +506,16 @@ TFS_HD uint64_t shl_mod(int64_t m, int sh) { return sh >= 64 ? 0 : ((uint64_t)m 
 // The tail of Algorithm 1.2 (Two-Sum) by its six native operations.
 TFS_HD double literal_sum_err(double a, double b, double s) {
 #if defined(__CUDA_ARCH__)
-    const double bv = __dsub_rn(s, a), av = __dsub_rn(s, bv);
-    return __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+    double t;
+    asm volatile(
+        "{\n\t.reg .f64 bv, av, ar, br;\n\t"
+        "sub.rn.f64 bv, %3, %1;\n\t"
+        "sub.rn.f64 av, %3, bv;\n\t"
+        "sub.rn.f64 ar, %1, av;\n\t"
+        "sub.rn.f64 br, %2, bv;\n\t"
+        "add.rn.f64 %0, ar, br;\n\t}"
+        : "=d"(t) : "d"(a), "d"(b), "d"(s));
+    return t;
 #else
     volatile double bv = s - a;
     volatile double av = s - bv;

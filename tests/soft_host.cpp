@@ -253,6 +253,24 @@ int64_t check_sqrt_near(uint64_t key, int64_t n, double *bad) {
     return nbad;
 }
 
+// RN(|z| 2^k) from bits against the CPU's ldexp-free multiplication.
+int64_t check_scale_pow2(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double z = rnd(key, i, 0, 2047);
+        int k = -(int)(mix(key + i) % 1100);
+        volatile double t = std::ldexp(1.0, k < -1022 ? -1022 : k);
+        if (k < -1022) continue;
+        volatile double ref = std::fabs(z) * t;
+        uint64_t got = scale_abs_pow2(d2u(z), k);
+        if (!same(u2d(got), ref)) {
+            if (!nbad) { bad[0] = z; bad[1] = (double)k; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 // Perfect squares and their neighbours.
 int64_t check_sqrt_hard(uint64_t key, int64_t n, double *bad) {
     int64_t nbad = 0;

@@ -24,7 +24,7 @@ def H(tmp_path_factory):
         getattr(L, name).argtypes = [u64, i64, ctypes.c_int, ctypes.c_int, p]
         getattr(L, name).restype = i64
     for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared",
-                 "check_sqrt_near"):
+                 "check_sqrt_near", "check_scale_pow2"):
         getattr(L, name).argtypes = [u64, i64, p]
         getattr(L, name).restype = i64
     L.soft_div.argtypes = [d, d]
@@ -106,6 +106,10 @@ def test_add_matches_ieee(H):
     run(H, "check_add", 26, 1_000_000, 0, 2047)
     run(H, "check_add", 27, 500_000, 0, 60)          # subnormal and tiny
     run(H, "check_add", 28, 500_000, 2000, 2046)     # near overflow
+
+
+def test_pow2_scaling_of_thresholds(H):
+    run(H, "check_scale_pow2", 30, 2_000_000)
 
 
 def test_twice_matches_ieee(H):
