@@ -45,10 +45,10 @@ __device__ __forceinline__ void two_diff(double a, double b, double &d, double &
     t = from_bits(soft::sum_err_bits(bits_of(a), bits_of(b) ^ 0x8000000000000000ull, bits_of(d)));
 }
 
-// Algorithm 3 (Two-Product-FMA): p = a*b, e = fma(a, b, -p).
+// Algorithm 3 (Two-Product-FMA): p = a*b, e = fma(a, b, -p); both from one
+// integer product (soft::two_prod_rn, the same bits as the two native ops).
 __device__ __forceinline__ void two_prod(double a, double b, double &p, double &e) {
-    p = __dmul_rn(a, b);
-    e = __fma_rn(a, b, -p);
+    soft::two_prod_rn(a, b, p, e);
 }
 
 // Correctly rounded division and square root (integer pipes, IEEE bits).

@@ -386,6 +386,62 @@ TFS_HD double mul_rn(double a, double b) {
     return u2d(sign | (r >= inf ? inf : r));            // past the top binade: Inf
 }
 
+TFS_HD double native_fma(double a, double b, double c) {
+#if defined(__CUDA_ARCH__)
+    double r;
+    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(b), "d"(c));
+    return r;
+#else
+    volatile double r = std::fma(a, b, c);
+    return r;
+#endif
+}
+
+// Algorithm 3's pair from one integer product: p = RN(a b) and the exact
+// error e = a b - p, bit-identical to a multiplication and fma(a, b, -p).
+// The 106-bit product of the significands gives p by round to nearest even
+// and e as its low part minus the rounding (exact whenever it is not
+// subnormal; a zero error is +0, as the fused operation returns).  Zero,
+// Inf and NaN operands are resolved in integer form; subnormal operands,
+// products near either end of the range and errors below the normal range
+// use the native pair.
+TFS_HD void two_prod_rn(double a, double b, double &p, double &e) {
+    const uint64_t ua = d2u(a), ub = d2u(b);
+    const int fa = (int)((ua >> 52) & 0x7FF), fb = (int)((ub >> 52) & 0x7FF);
+    const int ef = fa + fb - 1023;
+    const uint64_t sign = (ua ^ ub) & kSign;
+    if ((unsigned)(fa - 1) >= 2046u || (unsigned)(fb - 1) >= 2046u || ef < 111 || ef > 2044) {
+        const uint64_t xa = ua & ~kSign, xb = ub & ~kSign, inf = 0x7FF0000000000000ull;
+        const uint64_t nan = 0x7FF8000000000000ull;
+        if (xa > inf || xb > inf) { p = u2d(nan); e = u2d(nan); return; }
+        if (xa == inf || xb == inf) {
+            p = u2d((xa == 0 || xb == 0) ? nan : (sign | inf));
+            e = u2d(nan);
+            return;
+        }
+        if (xa == 0 || xb == 0) { p = u2d(sign); e = 0.0; return; }
+        p = native_mul(a, b);
+        e = native_fma(a, b, u2d(d2u(p) ^ kSign));
+        return;
+    }
+    const uint64_t ma = (ua & kFrac) | kHid, mb = (ub & kFrac) | kHid;
+    const uint64_t hi = mulhi(ma << 11, mb << 11), lo = (ma << 11) * (mb << 11);   // P 2^22
+    const int top = (int)(hi >> 63);                     // P in [2^105, 2^106)
+    const int gb = 10 + top;
+    uint64_t q = hi >> gb;
+    const uint64_t rem = hi & ((1ull << gb) - 1), half = 1ull << (gb - 1);
+    q += (rem > half) | ((rem == half) & ((lo != 0) | (q & 1)));
+    p = u2d(sign | (((uint64_t)(ef + top - 1) << 52) + q));
+    // e = P - q 2^(52+top) in units of 2^(ef-1127); |e| <= 2^(51+top): exact mod 2^64
+    const int64_t ei = (int64_t)(ma * mb - (q << (52 + top)));
+    if (ei == 0) { e = 0.0; return; }
+    const uint64_t se = sign ^ (ei < 0 ? kSign : 0);
+    const uint64_t mag = (uint64_t)(ei < 0 ? -ei : ei);
+    const int lz = clz64(mag);
+    const int lead = 63 - lz + ef - 1127;                // exponent of e's leading bit, >= -1016
+    e = u2d(se | ((uint64_t)(lead + 1023) << 52) | (((mag << lz) >> 11) & kFrac));
+}
+
 // Correctly rounded a + b.  Normal operands run on the integer pipes: the
 // significands aligned in 64-bit words with 10 guard bits, the bits shifted
 // out of the smaller operand jammed into its lowest bit (sticky), exact

@@ -271,6 +271,25 @@ int64_t check_scale_pow2(uint64_t key, int64_t n, double *bad) {
     return nbad;
 }
 
+// Two-Product pair against the CPU's multiplication and fma(a, b, -p).
+int64_t check_two_prod(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
+        if (i % 9 == 0) b = std::ldexp(1.0, (int)(i % 40) - 20);        // exact products
+        if (i % 13 == 0) a = 0.0;
+        volatile double pr = a * b;
+        volatile double er = std::fma(a, b, -pr);
+        double p, e;
+        two_prod_rn(a, b, p, e);
+        if (!same(p, pr) || !same(e, er)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 // Perfect squares and their neighbours.
 int64_t check_sqrt_hard(uint64_t key, int64_t n, double *bad) {
     int64_t nbad = 0;
