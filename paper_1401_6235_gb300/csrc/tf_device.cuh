@@ -123,19 +123,22 @@ __device__ __forceinline__ d2 mtf11(double x0, double x1, double y0) {
 // significand of z0, whose reciprocal square-root estimate the square root
 // already produced.  Every quotient is still the correctly rounded one.
 
+// The remainder fma(-z0, y0, x0) of Algorithm 4 comes packed from the
+// integer division's own exact remainder (soft::div_rn_y, same bits).
+
 // DTF1.1.1: z0 = x0/y0; r1 = fma(-z0, y0, x0); z1 = r1/y0.
 __device__ __forceinline__ d2 dtf111(double x0, double y0) {
     const uint64_t yb = soft::recip_of(y0);
-    const double q = soft::div_rn_y(x0, y0, yb);
-    const double r = __fma_rn(-q, y0, x0);
+    double r;
+    const double q = soft::div_rn_y(x0, y0, yb, &r);
     return {q, soft::div_rn_y(r, y0, yb)};
 }
 
 // DTF1.1: z0 = x0/y0; r = fma(-z0, y0, x0); c = r + x1; z1 = c/y0.
 __device__ __forceinline__ d2 dtf11(double x0, double x1, double y0) {
     const uint64_t yb = soft::recip_of(y0);
-    const double q = soft::div_rn_y(x0, y0, yb);
-    const double r = __fma_rn(-q, y0, x0);
+    double r;
+    const double q = soft::div_rn_y(x0, y0, yb, &r);
     return {q, soft::div_rn_y(__dadd_rn(r, x1), y0, yb)};
 }
 
@@ -143,8 +146,8 @@ __device__ __forceinline__ d2 dtf11(double x0, double x1, double y0) {
 //       c0 = r0 + r1; d0 = y0 + y1; z1 = c0/d0.
 __device__ __forceinline__ d2 dtf1(double x0, double x1, double y0, double y1) {
     const uint64_t yb = soft::recip_of(y0);
-    const double q = soft::div_rn_y(x0, y0, yb);
-    const double r0 = __fma_rn(-q, y0, x0);
+    double r0;
+    const double q = soft::div_rn_y(x0, y0, yb, &r0);
     const double r1 = __fma_rn(-q, y1, x1);
     const double c0 = __dadd_rn(r0, r1);
     const double d0 = __dadd_rn(y0, y1);
@@ -178,8 +181,8 @@ __device__ __forceinline__ d2 rtf1(double x0, double x1) {
     const double z0 = soft::sqrt_rn_y(x0, &yz);
     double u0, u1;
     two_sum(x0, x1, u0, u1);
-    const double v0 = soft::sqrt_rn_near(u0, x0, yz);       // RPF1 on (u0, u1)
-    const double d = __fma_rn(-v0, v0, u0);
+    double d;                                                // fma(-v0, v0, u0), packed
+    const double v0 = soft::sqrt_rn_near(u0, x0, yz, &d);   // RPF1 on (u0, u1)
     const double v1 = soft::div_rn(__dadd_rn(u1, d), twice(v0));
     const d2 w = stf11(v0, v1, z0);
     return {z0, __dadd_rn(w.z0, w.z1)};

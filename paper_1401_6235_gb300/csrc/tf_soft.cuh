@@ -164,6 +164,17 @@ TFS_HD double native_add(double a, double b) {
 #endif
 }
 
+TFS_HD double native_fma(double a, double b, double c) {
+#if defined(__CUDA_ARCH__)
+    double r;
+    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(b), "d"(c));
+    return r;
+#else
+    volatile double r = std::fma(a, b, c);
+    return r;
+#endif
+}
+
 // A seed y = m * 2^(e-150) (m the 24-bit significand, e the biased
 // exponent) for w in (1, 2] as the fixed-point value w 2^63 = m << (e - bias);
 // a seed at or above w = 2 (shift 41) saturates to 2^64 - 1.
@@ -224,17 +235,33 @@ TFS_HD uint64_t signif(double b) { return (d2u(b) & kFrac) | kHid; }
 // Reciprocal of b's significand for div_rn_y; any normal b.
 TFS_HD uint64_t recip_of(double b) { return recip1(signif(b)); }
 
+// Bits of the exact value v 2^scale for a signed integer |v| < 2^54 with at
+// most 53 significant bits; false when the value would not be a normal
+// binary64 (the caller then uses the native operation).  v = 0 gives +0.
+TFS_HD bool pack_exact(int64_t v, int scale, uint64_t *out) {
+    if (v == 0) { *out = 0; return true; }
+    const uint64_t sign = v < 0 ? kSign : 0;
+    const uint64_t mag = (uint64_t)(v < 0 ? -v : v);
+    const int lz = clz64(mag);
+    const int lead = 63 - lz + scale;
+    if (lead < -1022 || lead > 1023) return false;
+    *out = sign | ((uint64_t)(lead + 1023) << 52) | (((mag << lz) >> 11) & kFrac);
+    return true;
+}
+
 // Correctly rounded a / b given y, an estimate of 2^116 / signif(b) with
 // relative error below 2^-52 (recip_of(b), or the reciprocal square root of
 // sqrt_rn_y when b is twice that root), or 0 to compute it here: the
 // quotient estimate is then within two units and the remainder corrections
 // below restore the exact quotient.
-TFS_HD double div_rn_y(double a, double b, uint64_t y_in);
+// With rem != nullptr, *rem also receives RN(a - q b) for the returned q,
+// the bits of fma(-q, b, a) (Algorithm 4's exact remainder).
+TFS_HD double div_rn_y(double a, double b, uint64_t y_in, double *rem = nullptr);
 
 // Correctly rounded a / b.
 TFS_HD double div_rn(double a, double b) { return div_rn_y(a, b, 0); }
 
-TFS_HD double div_rn_y(double a, double b, uint64_t y_in) {
+TFS_HD double div_rn_y(double a, double b, uint64_t y_in, double *rem) {
     const uint64_t ua = d2u(a), ub = d2u(b);
     const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
     const int ed = ea - eb;
@@ -246,11 +273,14 @@ TFS_HD double div_rn_y(double a, double b, uint64_t y_in) {
         // subnormal operands and quotients near the range limits go native.
         const uint64_t xa = ua & ~kSign, xb = ub & ~kSign, inf = 0x7FF0000000000000ull;
         const uint64_t sign = (ua ^ ub) & kSign;
+        double q;
         if (xa > inf || xb > inf || (xa == inf && xb == inf) || (xa == 0 && xb == 0))
-            return u2d(0x7FF8000000000000ull);
-        if (xa == inf || xb == 0) return u2d(sign | inf);
-        if (xa == 0 || xb == inf) return u2d(sign);
-        return native_div(a, b);
+            q = u2d(0x7FF8000000000000ull);
+        else if (xa == inf || xb == 0) q = u2d(sign | inf);
+        else if (xa == 0 || xb == inf) q = u2d(sign);
+        else q = native_div(a, b);
+        if (rem) *rem = native_fma(u2d(d2u(q) ^ kSign), b, a);
+        return q;
     }
     const uint64_t ma = (ua & kFrac) | kHid, mb = (ub & kFrac) | kHid;
     const int sh = ma < mb;                              // quotient of significands < 1
@@ -273,9 +303,18 @@ TFS_HD double div_rn_y(double a, double b, uint64_t y_in) {
     // round to nearest, ties to even (2r == mb cannot occur for binary64
     // significands, but the rule is kept complete)
     const uint64_t r2 = r << 1;
-    q += (r2 > mb) | ((r2 == mb) & (q & 1));
+    const uint64_t up = (r2 > mb) | ((r2 == mb) & (q & 1));
+    q += up;
     const uint64_t sign = (ua ^ ub) & kSign;
-    return u2d(sign | (((uint64_t)(ed + 1022 - sh) << 52) + q));
+    const double quo = u2d(sign | (((uint64_t)(ed + 1022 - sh) << 52) + q));
+    if (rem) {
+        // a - q b = (N - q mb) 2^(Ea - 104 - sh), sign of a; N - q mb = r, or r - mb after rounding up
+        const int64_t rs = up ? (int64_t)r - (int64_t)mb : (int64_t)r;
+        uint64_t rb;
+        if (pack_exact(rs, ea - 1023 - 104 - sh, &rb)) *rem = u2d(rb ^ (rs != 0 ? (ua & kSign) : 0));
+        else *rem = native_fma(u2d(d2u(quo) ^ kSign), b, a);
+    }
+    return quo;
 }
 
 // Correctly rounded sqrt(a); *y_out receives 1/sqrt(m) as w 2^63 (m the
@@ -386,17 +425,6 @@ TFS_HD double mul_rn(double a, double b) {
     return u2d(sign | (r >= inf ? inf : r));            // past the top binade: Inf
 }
 
-TFS_HD double native_fma(double a, double b, double c) {
-#if defined(__CUDA_ARCH__)
-    double r;
-    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(b), "d"(c));
-    return r;
-#else
-    volatile double r = std::fma(a, b, c);
-    return r;
-#endif
-}
-
 // Algorithm 3's pair from one integer product: p = RN(a b) and the exact
 // error e = a b - p, bit-identical to a multiplication and fma(a, b, -p).
 // The 106-bit product of the significands gives p by round to nearest even
@@ -502,14 +530,18 @@ TFS_HD double add_rn(double a, double b) {
 // 2^-44 of u's reciprocal root: the root estimate is within 2^9 units, one
 // remainder-driven step brings it within two units, and the exact integer
 // remainder finishes as in sqrt_rn_y.  Otherwise the full routine runs.
-TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx) {
+// With rem != nullptr, *rem also receives RN(u - v^2) for the returned root
+// v, the bits of fma(-v, v, u) (Algorithm 5's exact residual).
+TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx, double *rem = nullptr) {
     const uint64_t uu = d2u(u), ux = d2u(x);
     const int f = (int)(uu >> 52);
     const uint64_t mu = (uu & kFrac) | kHid, mx = (ux & kFrac) | kHid;
     const uint64_t diff = mu > mx ? mu - mx : mx - mu;
     if (yx == 0 || f != (int)(ux >> 52) || (unsigned)(f - 1) >= 2046u || diff > 256) {
         uint64_t y;
-        return sqrt_rn_y(u, &y);
+        const double v = sqrt_rn_y(u, &y);
+        if (rem) *rem = native_fma(u2d(d2u(v) ^ kSign), v, u);
+        return v;
     }
     const int odd = f & 1;
     const int s = odd ? 52 : 53;
@@ -527,9 +559,17 @@ TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx) {
     if (rr < 0) { q -= 1; rr += (int64_t)(2 * q + 1); }
     if (rr > (int64_t)(2 * q)) { rr -= (int64_t)(2 * q + 1); q += 1; }
     if (rr > (int64_t)(2 * q)) { rr -= (int64_t)(2 * q + 1); q += 1; }
-    q += (uint64_t)(rr > (int64_t)q);
+    const bool up = rr > (int64_t)q;
     const int fr = (f + 1022 + odd) >> 1;
-    return u2d(((uint64_t)(fr - 1) << 52) + q);
+    const double v = u2d(((uint64_t)(fr - 1) << 52) + q + (uint64_t)up);
+    if (rem) {
+        // u - v^2 = (M - Q^2) 2^(2 er - 104), Q the returned significand
+        const int64_t rs = up ? rr - (int64_t)(2 * q + 1) : rr;
+        uint64_t rb;
+        if (pack_exact(rs, 2 * (fr - 1023) - 104, &rb)) *rem = u2d(rb);
+        else *rem = native_fma(u2d(d2u(v) ^ kSign), v, u);
+    }
+    return v;
 }
 
 // RN(|z| 2^k) as bits for an integer k <= 0 (the scaling of a panic
@@ -600,6 +640,14 @@ TFS_HD double sum_err(double a, double b, double s) { return u2d(sum_err_bits(d2
 // sign bit without the compiler forming a floating-point negation).
 TFS_HD uint64_t sum_err_bits(uint64_t ua, uint64_t ub, uint64_t us) {
     const unsigned fa = (unsigned)((ua >> 52) & 0x7FF), fb = (unsigned)((ub >> 52) & 0x7FF);
+    // Sterbenz: opposite signs, normal, magnitudes within a factor of two ->
+    // a + b is exact and the tail is +0 (doubling a normal magnitude below
+    // the top binade adds 2^52 to its bits)
+    {
+        const uint64_t xa = ua & ~kSign, xb = ub & ~kSign;
+        if (((ua ^ ub) >> 63) && fa - 1u < 2044u && fb - 1u < 2044u && xa <= xb + kHid && xb <= xa + kHid)
+            return 0;
+    }
     if ((fa >= 2045) | (fb >= 2045)) {
         // an Inf or NaN operand makes every variant of the literal sequence NaN
         if ((fa == 0x7FF) | (fb == 0x7FF)) return 0x7FF8000000000000ull;

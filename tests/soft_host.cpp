@@ -290,6 +290,31 @@ int64_t check_two_prod(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
     return nbad;
 }
 
+// Remainders packed from the integer division / root against fma.
+int64_t check_remainders(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
+        double r;
+        double q = div_rn_y(a, b, 0, &r);
+        volatile double qr = a / b;
+        volatile double rr = std::fma(-qr, b, a);
+        double x = std::fabs(a);
+        uint64_t y;
+        (void)sqrt_rn_y(x, &y);
+        double u = u2d(d2u(x) + (int64_t)(i % 401) - 200);
+        double d;
+        double v = sqrt_rn_near(u, x, y, &d);
+        volatile double vr = std::sqrt(u);
+        volatile double dr = std::fma(-vr, vr, u);
+        if (!same(q, qr) || !same(r, rr) || !same(v, vr) || !same(d, dr)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 // Perfect squares and their neighbours.
 int64_t check_sqrt_hard(uint64_t key, int64_t n, double *bad) {
     int64_t nbad = 0;

@@ -20,7 +20,7 @@ def H(tmp_path_factory):
     L = ctypes.CDLL(str(so))
     d, i64, u64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
     for name in ("check_div", "check_sqrt", "check_sum_err", "check_diff_err", "check_twice", "check_mul",
-                 "check_add", "check_two_prod"):
+                 "check_add", "check_two_prod", "check_remainders"):
         getattr(L, name).argtypes = [u64, i64, ctypes.c_int, ctypes.c_int, p]
         getattr(L, name).restype = i64
     for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared",
@@ -106,6 +106,12 @@ def test_two_prod_matches_mul_and_fma(H):
     run(H, "check_two_prod", 32, 1_000_000, 0, 2047)
     run(H, "check_two_prod", 33, 500_000, 500, 620)      # errors near the subnormal range
     run(H, "check_two_prod", 34, 500_000, 1500, 1550)    # products near overflow
+
+
+def test_packed_remainders_match_fma(H):
+    run(H, "check_remainders", 35, 2_000_000, 900, 1150)
+    run(H, "check_remainders", 36, 1_000_000, 0, 2047)
+    run(H, "check_remainders", 37, 500_000, 1, 120)      # remainders near the subnormal range
 
 
 def test_add_matches_ieee(H):
