@@ -273,12 +273,24 @@ TFS_HD double div_rn_y(double a, double b, uint64_t y_in, double *rem) {
         // subnormal operands and quotients near the range limits go native.
         const uint64_t xa = ua & ~kSign, xb = ub & ~kSign, inf = 0x7FF0000000000000ull;
         const uint64_t sign = (ua ^ ub) & kSign;
-        double q;
-        if (xa > inf || xb > inf || (xa == inf && xb == inf) || (xa == 0 && xb == 0))
-            q = u2d(0x7FF8000000000000ull);
-        else if (xa == inf || xb == 0) q = u2d(sign | inf);
-        else if (xa == 0 || xb == inf) q = u2d(sign);
-        else q = native_div(a, b);
+        // The remainder fma(-q, b, a) of these cases is NaN (an Inf or NaN
+        // operand, or a zero divisor: Inf - Inf or 0 * Inf) except for a zero
+        // dividend over a finite nonzero divisor, where -q b and a are zeros
+        // of opposite signs and the sum is +0 (a zero over Inf: 0 * Inf).
+        const uint64_t nan = 0x7FF8000000000000ull;
+        if (xa > inf || xb > inf || (xa == inf && xb == inf) || (xa == 0 && xb == 0)) {
+            if (rem) *rem = u2d(nan);
+            return u2d(nan);
+        }
+        if (xa == inf || xb == 0) {
+            if (rem) *rem = u2d(nan);
+            return u2d(sign | inf);
+        }
+        if (xa == 0 || xb == inf) {
+            if (rem) *rem = u2d(xa == 0 && xb != inf ? 0 : nan);
+            return u2d(sign);
+        }
+        const double q = native_div(a, b);
         if (rem) *rem = native_fma(u2d(d2u(q) ^ kSign), b, a);
         return q;
     }
@@ -540,7 +552,14 @@ TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx, double *rem = nullpt
     if (yx == 0 || f != (int)(ux >> 52) || (unsigned)(f - 1) >= 2046u || diff > 256) {
         uint64_t y;
         const double v = sqrt_rn_y(u, &y);
-        if (rem) *rem = native_fma(u2d(d2u(v) ^ kSign), v, u);
+        if (rem) {
+            // fma(-v, v, u) without a native operation where the root is NaN
+            // (NaN), +Inf (-Inf + Inf: NaN) or a zero (v = u, -u u + u = u)
+            const uint64_t xu = uu & ~kSign, inf = 0x7FF0000000000000ull;
+            if ((uu >> 63 && xu != 0) || xu >= inf) *rem = u2d(0x7FF8000000000000ull);
+            else if (xu == 0) *rem = u;
+            else *rem = native_fma(u2d(d2u(v) ^ kSign), v, u);
+        }
         return v;
     }
     const int odd = f & 1;
@@ -640,14 +659,6 @@ TFS_HD double sum_err(double a, double b, double s) { return u2d(sum_err_bits(d2
 // sign bit without the compiler forming a floating-point negation).
 TFS_HD uint64_t sum_err_bits(uint64_t ua, uint64_t ub, uint64_t us) {
     const unsigned fa = (unsigned)((ua >> 52) & 0x7FF), fb = (unsigned)((ub >> 52) & 0x7FF);
-    // Sterbenz: opposite signs, normal, magnitudes within a factor of two ->
-    // a + b is exact and the tail is +0 (doubling a normal magnitude below
-    // the top binade adds 2^52 to its bits)
-    {
-        const uint64_t xa = ua & ~kSign, xb = ub & ~kSign;
-        if (((ua ^ ub) >> 63) && fa - 1u < 2044u && fb - 1u < 2044u && xa <= xb + kHid && xb <= xa + kHid)
-            return 0;
-    }
     if ((fa >= 2045) | (fb >= 2045)) {
         // an Inf or NaN operand makes every variant of the literal sequence NaN
         if ((fa == 0x7FF) | (fb == 0x7FF)) return 0x7FF8000000000000ull;

@@ -333,4 +333,37 @@ int64_t check_sqrt_hard(uint64_t key, int64_t n, double *bad) {
     return nbad;
 }
 
+// Remainders of the special cases (zeros, Inf, NaN, subnormals, extremes):
+// every ordered pair of a fixed list, for the division and for the root of
+// u started from x's reciprocal root (sqrt_rn_near falls back on its own).
+int64_t check_remainder_specials(uint64_t key, int64_t n, double *bad) {
+    (void)key;
+    (void)n;
+    const double inf = INFINITY, big = 1.7976931348623157e308, tiny = 4.9406564584124654e-324;
+    const double vals[] = {0.0, -0.0, inf, -inf, NAN, -NAN, 1.0, -1.0, 3.0, -0.75, big, -big, tiny, -tiny,
+                           2.2250738585072014e-308, 1e-310, -3e-320, 2.0, 0.5, 1e300, -1e-300};
+    const int nv = (int)(sizeof(vals) / sizeof(vals[0]));
+    int64_t nbad = 0;
+    for (int i = 0; i < nv; ++i) {
+        for (int j = 0; j < nv; ++j) {
+            const double a = vals[i], b = vals[j];
+            double r;
+            const double q = div_rn_y(a, b, 0, &r);
+            volatile double qr = a / b;
+            volatile double rr = std::fma(-qr, b, a);
+            uint64_t y;
+            (void)sqrt_rn_y(b, &y);
+            double d;
+            const double v = sqrt_rn_near(a, b, y, &d);
+            volatile double vr = std::sqrt(a);
+            volatile double dr = std::fma(-vr, vr, a);
+            if (!same(q, qr) || !same(r, rr) || !same(v, vr) || !same(d, dr)) {
+                if (!nbad) { bad[0] = a; bad[1] = b; }
+                ++nbad;
+            }
+        }
+    }
+    return nbad;
+}
+
 }  // extern "C"

@@ -24,7 +24,7 @@ def H(tmp_path_factory):
         getattr(L, name).argtypes = [u64, i64, ctypes.c_int, ctypes.c_int, p]
         getattr(L, name).restype = i64
     for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared",
-                 "check_sqrt_near", "check_scale_pow2"):
+                 "check_sqrt_near", "check_scale_pow2", "check_remainder_specials"):
         getattr(L, name).argtypes = [u64, i64, p]
         getattr(L, name).restype = i64
     L.soft_div.argtypes = [d, d]
@@ -112,6 +112,7 @@ def test_packed_remainders_match_fma(H):
     run(H, "check_remainders", 35, 2_000_000, 900, 1150)
     run(H, "check_remainders", 36, 1_000_000, 0, 2047)
     run(H, "check_remainders", 37, 500_000, 1, 120)      # remainders near the subnormal range
+    run(H, "check_remainder_specials", 0, 0)             # zeros, Inf, NaN, subnormals, extremes
 
 
 def test_add_matches_ieee(H):
