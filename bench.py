@@ -283,7 +283,8 @@ def workload_dot(args, rank, world, dist_on):
         gx.copy_(hx, non_blocking=True)
         gy.copy_(hy, non_blocking=True)
         T.twofold_dot(gx, gy, out=out, ws=ws)
-        hres[:2].copy_(torch.cat([out[0], out[1]]), non_blocking=True)
+        hres[0:1].copy_(out[0], non_blocking=True)
+        hres[1:2].copy_(out[1], non_blocking=True)
 
     e2e_ms = time_steps(e2e_step, args.steps, args.warmup, dist_on)
     per = ms / args.steps
@@ -297,7 +298,7 @@ def workload_dot(args, rank, world, dist_on):
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_ms / args.steps * 1e3, "unit": "us", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 16},
-        "gpu_launches": args.steps, "clocks": cs.summary(),
+        "gpu_launches": 2 * args.steps, "clocks": cs.summary(),    # leaves kernel + final tree
         "_kernel_ms": per, "_ops": DOT_OPS * n, "_bytes": DOT_BYTES * n,
         "_sample": lambda: cpu_sample_dot(n),
     }
@@ -320,7 +321,8 @@ def workload_cond_dots(args, rank, world, dist_on):
     import torch
     import paper_1401_6235_gb300 as T
     import synth
-    nj, n = 4096, 1 << 16
+    n = 1 << 16
+    nj = max(1, args.n // n) if args.n else 4096
     x, y, offs, exact, cond, _ = synth.cond_dots(nj, n, seed=rank)
     gx, gy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
     ws = T.workspace(T.lib().twofold_workspace_bytes(T.KIND_DOT, nj * n, nj, None))
@@ -334,11 +336,11 @@ def workload_cond_dots(args, rank, world, dist_on):
                           dist_on)
     per = ms / args.steps
     return {
-        "metric": "batched twofold dots jobs/s (4096 x 2^16)", "value": nj * world / (per * 1e-3),
+        "metric": f"batched twofold dots jobs/s ({nj} x 2^16)", "value": nj * world / (per * 1e-3),
         "unit": "jobs/s", "ms_per_step": per, "plain_ms_per_step": plain_ms / args.steps,
         "slowdown_vs_plain": per / (plain_ms / args.steps), "gbs": DOT_BYTES * nj * n / (per * 1e-3) / 1e9,
-        "config": {"workload": "4096 ill-conditioned dots x 2^16, cond 10^U(2,30)", "n": nj * n,
-                   "l2": "inputs (4 GiB) larger than L2", "parallelism": f"replicas x{world}"},
+        "config": {"workload": f"{nj} ill-conditioned dots x 2^16, cond 10^U(2,30)", "n": nj * n,
+                   "l2": f"inputs ({nj * n * 16 / 2**30:g} GiB) larger than L2", "parallelism": f"replicas x{world}"},
         "gpu_launches": args.steps, "clocks": cs.summary(),
         "_kernel_ms": per, "_ops": DOT_OPS * nj * n, "_bytes": DOT_BYTES * nj * n, "_sample": None,
     }

@@ -48,6 +48,25 @@ inline int launch_status() {
     return e == cudaSuccess ? TF_OK : TF_ECUDA;
 }
 
+// Launch with programmatic stream serialization: the kernel may begin while
+// its predecessor in the stream finishes, and must call griddepcontrol.wait
+// before it touches memory that the predecessor may write or read.
+template <typename Arg>
+inline cudaError_t launch_pdl(void (*kernel)(Arg), int64_t grid, int block, size_t smem, cudaStream_t s,
+                              const Arg &a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 inline int sm_count() {
     static int sms = 0;
     if (sms == 0) {

@@ -21,7 +21,7 @@ namespace {
 constexpr int kThreads = 256;        // = maximum leaves per block
 constexpr int kInlineJobs = 32;      // job tables up to this size travel in the launch params
 constexpr int64_t kLatMaxLeaves = 2048;   // latency schedule: at most this many leaves in all
-constexpr int64_t kLatMaxLeaf = 1024;     // ... each at most this long (4 L doubles of shared memory)
+constexpr int64_t kLatMaxLeaf = 2048;     // ... each at most this long (one CTA holds B L <= 2048)
 
 struct Tab {
     const int64_t *offs;   // device job table (njobs+1), or nullptr: use the inline copy
@@ -64,6 +64,14 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while its predecessor in the
+// stream finishes; griddep_wait() blocks until that predecessor has completed
+// and its memory is visible (a no-op for an ordinary launch), and
+// griddep_release() lets the successor start launching.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // One element of a leaf: acc = ATF1(acc, term) (ATF1.1 for a dotted sum).
 template <bool DOT, bool PLAIN>
 __device__ __forceinline__ void leaf_step(tf::d2 &acc, double x0, double x1, bool xd, double y0, double y1,
@@ -104,6 +112,8 @@ template <bool DOT, bool PLAIN, bool STAGED>
 __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant__ RedArgs A) {
     extern __shared__ double stage[];                // [2][narr][B][C+1] when STAGED
     __shared__ double s0[kThreads], s1[kThreads];
+    griddep_wait();
+    griddep_release();
     const int t = threadIdx.x;
     const int64_t b = blockIdx.x;
     const int j = job_of(A.tab, A.njobs, b);
@@ -187,70 +197,219 @@ __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant_
     }
 }
 
-// Latency schedule for jobs with few leaves: one CTA per leaf (B = 1).
-// The leaf's left-to-right accumulation acc = ATF1(acc, term_i) is split
-// into its independent and its sequential parts, in this order:
-//   terms (p_i, e_i) of all elements        - all threads, in parallel
-//   z0 chain  a_i = acc0, acc0 = acc0 + p_i  - one thread (one FP64 add per step)
-//   tails     t_i = Two-Sum tail(a_i, p_i)   - all threads, in parallel
-//   z1 chain  acc1 = (acc1 + e_i) + t_i      - one thread (acc1 + t_i for ATF1.1)
-// Every operation and operand is the one the sequential leaf uses, so the
-// bits are the same; a lane-serial FP64 chain costs a full warp slot per
-// operation on this GPU, so only the two chains stay serial.
+// Named barriers for the chunk hand-overs of reduce_lat (ids 1..2 kLatChunks;
+// id 0 is __syncthreads).
+constexpr int kLatChunks = 7;
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_wait(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Latency schedule for jobs with few leaves.  A CTA takes an aligned block
+// of B leaves (B L <= kLatElems; one warp lane per leaf) and splits each
+// leaf's left-to-right accumulation acc = ATF1(acc, term_i) into its
+// independent and its sequential parts:
+//   terms (p_i, e_i) of all B leaves    - all threads (kLatPer loads each, in flight together)
+//   z0 chain  s_i = s_{i-1} + p_i        - warp 0, lane l = leaf l; it keeps only
+//                                          the checkpoints s_{8k+7}
+//   tails     s_{8k..8k+7} again from the checkpoint s_{8k-1} (the same adds
+//             in the same order, so the same bits) and
+//             t_i = Two-Sum tail(s_{i-1}, p_i, s_i), in place of p_i
+//                                        - warps 2.., one lane per 8 steps of a leaf
+//   z1 chain  acc1 = (acc1 + e_i) + t_i  - warp 1, lane l (acc1 + t_i for ATF1.1)
+// then the block's subtree of the pairwise tree by warp shuffles.  Every
+// operation and operand is the one the sequential leaf uses, so the bits are
+// the same.  On this GPU a dependent FP64 add costs ~64 cycles, a warp
+// issues one FP64 instruction per ~64 cycles whatever its active lanes, and
+// chains in different warps do not slow each other: so the B leaves share
+// the cost of one chain, and the chain warps issue little besides their adds
+// (a store behind each add would cost ~40 more cycles per step).  The three
+// stages form a pipeline over chunks of the leaf (a short first chunk, then
+// at most kLatChunks - 1 more): warp 0 hands a finished z0 chunk to the tail
+// warps, they hand its tails to warp 1, each through a named barrier
+// (bar.arrive / bar.sync; ids 1..kLatChunks and kLatChunks+1..2 kLatChunks,
+// each used once; every participant walks the same chunk count, so every
+// barrier completes).  The chains run in register blocks of 8 steps, and a
+// lane past the end of its (short, last) leaf adds -0.0, which leaves every
+// value unchanged.
+constexpr int kLatThreads = 512;
+constexpr int kLatPer = 4;                          // phase-1 elements per thread
+constexpr int kLatElems = kLatPer * kLatThreads;    // elements per CTA at most
+constexpr int kTailThreads = kLatThreads - 64;      // warps 2..
+constexpr int kLatFirst = 16;                       // length of the first chunk
+
+// Chunk c of a leaf of (rounded) length n8: [start, end), multiples of 8.
+__device__ __forceinline__ int lat_chunk_start(int c, int n8) {
+    if (c == 0) return 0;
+    const int first = min(kLatFirst, n8);
+    const int rest = n8 - first;
+    const int per = (((rest + kLatChunks - 2) / (kLatChunks - 1)) + 7) & ~7;
+    return min(n8, first + (c - 1) * per);
+}
+
 template <bool DOT, bool PLAIN>
-__global__ void __launch_bounds__(kThreads) reduce_lat(const __grid_constant__ RedArgs A) {
-    extern __shared__ double lat[];                  // P, E, A0, S (also T) : 4 x L
-    const int t = threadIdx.x;
+__global__ void __launch_bounds__(kLatThreads) reduce_lat(const __grid_constant__ RedArgs A) {
+    extern __shared__ double lat[];                  // PT, E : [B][L + 1]; CK : [B][L / 8 + 1]
+    __shared__ double r0[32];
+    griddep_wait();
+    griddep_release();
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int64_t b = blockIdx.x;
     const int j = job_of(A.tab, A.njobs, b);
     const int64_t e0 = A.tab.off(j), len = A.tab.off(j + 1) - e0;
-    const int64_t leaf = b - A.tab.b0(j);
-    const int64_t lb = e0 + leaf * A.L;
-    const int llen = (int)min(A.L, e0 + len - lb);
-    const int L = (int)A.L;
-    double *P = lat, *E = lat + L, *A0 = lat + 2 * L, *S = lat + 3 * L;
+    const int64_t m = (len + A.L - 1) / A.L;
+    const int64_t leaf0 = (b - A.tab.b0(j)) * A.B;
+    const int nl = (int)min((int64_t)A.B, m - leaf0);
+    const int64_t base = e0 + leaf0 * A.L, end = e0 + len;
+    const int L = (int)A.L, Sd = L + 1, Cd = L / 8 + 1;
+    const int nel = (int)min((int64_t)nl * L, end - base);   // elements of the block
+    double *PT = lat, *E = lat + (size_t)A.B * Sd, *CK = lat + 2 * (size_t)A.B * Sd;
     const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
-    for (int i = t; i < llen; i += kThreads) {
-        const int64_t g = lb + i;
-        if (PLAIN) {
-            P[i] = DOT ? __dmul_rn(A.xh[g], A.yh[g]) : A.xh[g];
-        } else if (DOT) {
-            const tf::d2 q = tf::apply(tf::OP_MUL, A.xh[g], xd ? 0.0 : A.xl[g], xd, A.yh[g],
-                                       yd ? 0.0 : A.yl[g], yd);
-            P[i] = q.z0;
-            E[i] = q.z1;
-        } else {
-            P[i] = A.xh[g];
-            if (!xd) E[i] = A.xl[g];
+    {
+        // element k of the block is element k - r L of leaf r = k / L
+        double xv[kLatPer], xlv[kLatPer], yv[kLatPer], ylv[kLatPer];
+#pragma unroll
+        for (int u = 0; u < kLatPer; ++u) {
+            const int k = t + u * kLatThreads;
+            xv[u] = xlv[u] = yv[u] = ylv[u] = 0.0;
+            if (k < nel) {
+                const int64_t g = base + k;
+                xv[u] = A.xh[g];
+                if (!xd) xlv[u] = A.xl[g];
+                if (DOT) {
+                    yv[u] = A.yh[g];
+                    if (!yd) ylv[u] = A.yl[g];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLatPer; ++u) {
+            const int k = t + u * kLatThreads;
+            if (k < nel) {
+                const int si = k + k / L;                    // r (L + 1) + i
+                if (PLAIN) {
+                    PT[si] = DOT ? __dmul_rn(xv[u], yv[u]) : xv[u];
+                } else if (DOT) {
+                    const tf::d2 q = tf::apply(tf::OP_MUL, xv[u], xlv[u], xd, yv[u], ylv[u], yd);
+                    PT[si] = q.z0;
+                    E[si] = q.z1;
+                } else {
+                    PT[si] = xv[u];
+                    if (!xd) E[si] = xlv[u];
+                }
+            }
         }
     }
     __syncthreads();
-    double acc0 = 0.0, acc1 = 0.0;
-    if (t == 0) {
-#pragma unroll 8
-        for (int i = 0; i < llen; ++i) {
-            if (!PLAIN) A0[i] = acc0;
-            acc0 = __dadd_rn(acc0, P[i]);
-            if (!PLAIN) S[i] = acc0;
+    // this lane's leaf (lanes >= nl idle); leaf 0 is the longest
+    const int my_len = lane < nl ? (int)min((int64_t)L, end - (base + (int64_t)lane * L)) : 0;
+    const int len0 = (int)min((int64_t)L, end - base);
+    const int n8 = (len0 + 7) & ~7;
+    tf::d2 acc = {0.0, 0.0};
+    if (PLAIN) {
+        if (warp == 0) {
+            const double *Pr = PT + lane * Sd;
+            for (int i = 0; i < n8; i += 8) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = i + u < my_len ? Pr[i + u] : -0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc.z0 = __dadd_rn(acc.z0, v[u]);
+            }
         }
-    }
-    if (!PLAIN) {
-        __syncthreads();
-        for (int i = t; i < llen; i += kThreads) S[i] = tf::soft::sum_err(A0[i], P[i], S[i]);   // S now holds t_i
-        __syncthreads();
-        const bool has_e = DOT || !xd;
-        if (t == 0) {
-#pragma unroll 8
-            for (int i = 0; i < llen; ++i)
-                acc1 = has_e ? __dadd_rn(__dadd_rn(acc1, E[i]), S[i]) : __dadd_rn(acc1, S[i]);
+    } else {
+        int nch = 1;
+        while (nch < kLatChunks && lat_chunk_start(nch, n8) < n8) ++nch;
+        if (warp == 0) {
+            const double *Pr = PT + lane * Sd;
+            double *Cr = CK + lane * Cd;
+            for (int c = 0; c < nch; ++c) {
+                const int i1 = lat_chunk_start(c + 1, n8);
+                for (int i = lat_chunk_start(c, n8); i < i1; i += 8) {
+                    double v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = i + u < my_len ? Pr[i + u] : -0.0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc.z0 = __dadd_rn(acc.z0, v[u]);
+                    if (lane < nl) Cr[i >> 3] = acc.z0;          // s_{i+7}
+                }
+                __syncwarp();
+                __threadfence_block();
+                bar_arrive(1 + c, 32 + kTailThreads);
+            }
+            r0[lane] = acc.z0;
+        } else if (warp >= 2) {
+            for (int c = 0; c < nch; ++c) {
+                bar_wait(1 + c, 32 + kTailThreads);
+                const int k0 = lat_chunk_start(c, n8) >> 3, nk = (lat_chunk_start(c + 1, n8) >> 3) - k0;
+                for (int task = t - 64; task < nl * nk; task += kTailThreads) {
+                    const int r = task / nk, k = k0 + task - r * nk;
+                    const int rl = (int)min((int64_t)L, end - (base + (int64_t)r * L));
+                    double *Pr = PT + r * Sd;
+                    double sv = k ? CK[r * Cd + k - 1] : 0.0;
+                    for (int i = 8 * k; i < min(8 * k + 8, rl); ++i) {
+                        const double p = Pr[i];
+                        const double sn = __dadd_rn(sv, p);
+                        Pr[i] = tf::soft::sum_err(sv, p, sn);             // t_i replaces p_i
+                        sv = sn;
+                    }
+                }
+                __threadfence_block();
+                bar_arrive(1 + kLatChunks + c, 32 + kTailThreads);
+            }
+        } else {   // warp 1
+            const bool has_e = DOT || !xd;
+            const double *Er = E + lane * Sd, *Tr = PT + lane * Sd;
+            for (int c = 0; c < nch; ++c) {
+                bar_wait(1 + kLatChunks + c, 32 + kTailThreads);
+                const int i1 = lat_chunk_start(c + 1, n8);
+                for (int i = lat_chunk_start(c, n8); i < i1; i += 8) {
+                    double ev[8], tv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const bool in = i + u < my_len;
+                        ev[u] = in && has_e ? Er[i + u] : -0.0;
+                        tv[u] = in ? Tr[i + u] : -0.0;
+                    }
+                    if (has_e) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(__dadd_rn(acc.z1, ev[u]), tv[u]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(acc.z1, tv[u]);
+                    }
+                }
+            }
         }
+        __syncthreads();
+        if (warp == 1) acc.z0 = r0[lane];
     }
-    if (t == 0) {
-        const tf::d2 r = {acc0, acc1};
-        if (A.tab.b0(j + 1) - A.tab.b0(j) == 1) write_result<PLAIN>(A, j, r);
-        else { A.part0[b] = r.z0; A.part1[b] = r.z1; }
+    // the block's subtree: node l of level k combines lanes l and l + 2^k
+    const int tw = PLAIN ? 0 : 1;
+    if (warp == tw) {
+        for (int st = 1; st < nl; st <<= 1) {
+            const double o0 = __shfl_down_sync(0xffffffffu, acc.z0, st);
+            const double o1 = __shfl_down_sync(0xffffffffu, acc.z1, st);
+            if ((lane & (2 * st - 1)) == 0 && lane + st < nl) acc = combine<PLAIN>(acc, {o0, o1});
+        }
+        if (lane == 0) {
+            if (A.tab.b0(j + 1) - A.tab.b0(j) == 1) write_result<PLAIN>(A, j, acc);
+            else { A.part0[b] = acc.z0; A.part1[b] = acc.z1; }
+        }
     }
 }
+
+// Leaves per CTA of the latency schedule: the largest power of two <= 32
+// with B L <= kLatElems (1 when L alone exceeds it).
+int lat_group(int64_t L) {
+    int B = 32;
+    while (B > 1 && (int64_t)B * L > kLatElems) B >>= 1;
+    return B;
+}
+
+size_t lat_smem(int B, int64_t L) { return ((size_t)2 * B * (L + 1) + (size_t)B * (L / 8 + 1)) * sizeof(double); }
 
 // One CTA per job with 0 or >= 2 blocks.  Thread t first reduces the aligned
 // group of G partials [tG, (t+1)G) in place (G = 2^g, G*kThreads >= nb),
@@ -258,6 +417,8 @@ __global__ void __launch_bounds__(kThreads) reduce_lat(const __grid_constant__ R
 template <bool PLAIN>
 __global__ void __launch_bounds__(kThreads) reduce_final(const __grid_constant__ RedArgs A) {
     __shared__ double s0[kThreads], s1[kThreads];
+    griddep_wait();
+    griddep_release();
     const int j = blockIdx.x, t = threadIdx.x;
     const int64_t p0 = A.tab.b0(j), nb = A.tab.b0(j + 1) - p0;
     if (nb == 1) return;
@@ -339,7 +500,7 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
     for (int j = 0; j < njobs; ++j) M += (offs[j + 1] - offs[j] + L - 1) / L;
     // few leaves of moderate length: the latency schedule, one CTA per leaf
     const bool lat = M <= kLatMaxLeaves && L <= kLatMaxLeaf;
-    const int B = lat ? 1 : leaves_per_block(M);
+    const int B = lat ? lat_group(L) : leaves_per_block(M);
     int64_t nblk = 0;
     bool need_final = false;
     for (int j = 0; j < njobs; ++j) {
@@ -387,24 +548,27 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
     A.C = chunk_of(B, A.narr, L);
     if (nblk > 0) {
         if (lat) {
-            const size_t smem = (size_t)4 * L * sizeof(double);
+            const size_t smem = lat_smem(B, L);
             if (smem > 48 * 1024 && cudaFuncSetAttribute(reduce_lat<DOT, PLAIN>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)smem) != cudaSuccess)
                 return TF_ECUDA;
-            reduce_lat<DOT, PLAIN><<<(unsigned)nblk, kThreads, smem, s>>>(A);
+            if (tfh::launch_pdl(reduce_lat<DOT, PLAIN>, nblk, kLatThreads, smem, s, A) != cudaSuccess) return TF_ECUDA;
         } else if (PLAIN) {
             const size_t smem = (size_t)2 * A.narr * B * (A.C + 1) * sizeof(double);
             if (smem > 48 * 1024 && cudaFuncSetAttribute(reduce_blocks<DOT, PLAIN, true>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)smem) != cudaSuccess)
                 return TF_ECUDA;
-            reduce_blocks<DOT, PLAIN, true><<<(unsigned)nblk, kThreads, smem, s>>>(A);
+            if (tfh::launch_pdl(reduce_blocks<DOT, PLAIN, true>, nblk, kThreads, smem, s, A) != cudaSuccess)
+                return TF_ECUDA;
         } else {
-            reduce_blocks<DOT, PLAIN, false><<<(unsigned)nblk, kThreads, 0, s>>>(A);
+            if (tfh::launch_pdl(reduce_blocks<DOT, PLAIN, false>, nblk, kThreads, 0, s, A) != cudaSuccess)
+                return TF_ECUDA;
         }
     }
-    if (need_final) reduce_final<PLAIN><<<njobs, kThreads, 0, s>>>(A);
+    if (need_final && tfh::launch_pdl(reduce_final<PLAIN>, njobs, kThreads, 0, s, A) != cudaSuccess)
+        return TF_ECUDA;
     return tfh::launch_status();
 }
 

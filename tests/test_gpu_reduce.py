@@ -69,6 +69,28 @@ def test_leaf_sizes(L):
     assert_bits(T.plain_dot(dev(x), dev(y), p=p), [O.reduce_plain(x, y, L=L)], "plain")
 
 
+@pytest.mark.parametrize("L,n", [(1, 2000), (3, 5003), (33, 40000), (256, 8191), (512, 300001), (1024, 1000000),
+                                 (2048, 300001)])
+def test_latency_schedule_leaf_sizes(L, n):
+    """Jobs of at most 2048 leaves of at most 2048 elements take the latency
+    schedule (up to 32 leaves and 2048 elements per CTA, one lane per leaf, ragged last
+    leaf and last block); dot with tails on one side, dotted sum, plain twins."""
+    x, y = synth.dot_uniform(n, seed=L + n)
+    xl = tails(x, L)
+    p = T.params(leaf=L)
+    e0, e1 = O.reduce(x, xl, y, None, L=L)
+    z0, z1, fl = T.twofold_dot(dev(x), dev(y), dev(xl), p=p)
+    assert_bits(z0, [e0], f"L={L} dot z0")
+    assert_bits(z1, [e1], f"L={L} dot z1")
+    assert_flags(fl, [O.flag(e0, e1)], f"L={L} dot flag")
+    s0, s1 = O.reduce(x, None, L=L)
+    q0, q1, _ = T.twofold_sum(dev(x), p=p)
+    assert_bits(q0, [s0], f"L={L} sum z0")
+    assert_bits(q1, [s1], f"L={L} sum z1")
+    assert_bits(T.plain_dot(dev(x), dev(y), p=p), [O.reduce_plain(x, y, L=L)], f"L={L} plain dot")
+    assert_bits(T.plain_sum(dev(x), p=p), [O.reduce_plain(x, L=L)], f"L={L} plain sum")
+
+
 def test_config_dot_65536_zero_tails_equal_dotted():
     """n = 65536 uniform[-1,1] seed 0: tails materialised as +0 and tails
     absent give the same bits, equal to the oracle."""
