@@ -17,6 +17,12 @@
  *    caller (for example torch tensors); the library never allocates, frees
  *    or synchronises.  Every call is asynchronous on `stream` (a
  *    cudaStream_t passed as void*; NULL is the legacy default stream).
+ *  - Pinned host memory that the device maps at the same address (memory
+ *    from cudaHostAlloc / cudaMallocHost under unified addressing;
+ *    twofold_host_mapped tells) may stand in for device memory in the data
+ *    arrays of twofold_ew and plain_ew: the kernels then read their inputs
+ *    and write their results across the host link themselves.  The
+ *    arithmetic is the same device code with the same bits.
  *  - Device data pointers must be 8-byte aligned (flags: any alignment).
  *    Lengths are element counts; n == 0 is valid, and then data pointers
  *    that would not be read or written may be NULL.
@@ -89,6 +95,13 @@ const char *twofold_strerror(int status);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int twofold_version(void);
+
+/* 1 when `ptr` is host memory that the current device accesses at the same
+ * address (page-locked and mapped, see the conventions above), else 0 (also
+ * for device memory, ordinary pageable memory, NULL, or when no device is
+ * present).  No paper counterpart: a query for the host-buffer form of the
+ * elementwise entry points.  Never fails; clears the CUDA error it may raise. */
+int twofold_host_mapped(const void *ptr);
 
 /* --------------------------------------------------- elementwise programs
  *

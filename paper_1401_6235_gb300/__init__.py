@@ -6,7 +6,9 @@ flag byte signals when z1 is large relative to z0.  All arithmetic runs in
 the CUDA kernels of ``libtwofold.so`` (C ABI declared in include/twofold.h);
 this module only marshals torch tensors (device memory, streams) into
 pointers and sizes.  There is no CPU fallback: importing works without a
-GPU, but every call needs the built library and CUDA tensors.
+GPU, but every call needs the built library and CUDA tensors (the
+elementwise calls also take pinned host tensors that the device maps, whose
+bytes the kernels then move across the host link themselves).
 """
 from __future__ import annotations
 
@@ -59,6 +61,7 @@ _IN, _OUT, _PP = tf_in, tf_out, ctypes.POINTER(tf_params)
 SIGNATURES = {
     "twofold_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "twofold_version": ([], ctypes.c_int),
+    "twofold_host_mapped": ([_P], ctypes.c_int),
     "twofold_ew": ([_P, _I32, _P, _I32, _I64, _OUT, _PP, _P], ctypes.c_int),
     "plain_ew": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
     "twofold_workspace_bytes": ([_I32, _I64, _I32, _PP], _SZ),
@@ -112,15 +115,20 @@ def _torch():
     return torch
 
 
-def _dev(t, name="tensor"):
-    """Device pointer of a contiguous CUDA float64/uint8 tensor (or None)."""
+def _dev(t, name="tensor", host_ok=False):
+    """Device pointer of a contiguous CUDA float64/uint8 tensor (or None).
+    With host_ok, a pinned host tensor that the device maps at the same
+    address is accepted too (the kernels access it across the host link)."""
     if t is None:
         return None
-    if not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor (the twofold path has no CPU fallback)")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
-    return t.data_ptr()
+    if t.is_cuda:
+        return t.data_ptr()
+    if host_ok and t.is_pinned() and lib().twofold_host_mapped(ctypes.c_void_p(t.data_ptr())) == 1:
+        return t.data_ptr()
+    raise ValueError(f"{name} must be a CUDA tensor{' or device-mapped pinned host tensor' if host_ok else ''} "
+                     "(the twofold path has no CPU fallback)")
 
 
 def _stream(stream):
@@ -155,6 +163,9 @@ def _outputs(n, device, out):
     torch = _torch()
     if out is not None:
         return out
+    if device.type == "cpu":        # host-buffer form: pinned, device-mapped outputs
+        return (torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory(),
+                torch.empty(n, dtype=torch.uint8).pin_memory())
     return (torch.empty(n, dtype=torch.float64, device=device),
             torch.empty(n, dtype=torch.float64, device=device),
             torch.empty(n, dtype=torch.uint8, device=device))
@@ -170,16 +181,18 @@ def _prog_array(prog):
 def twofold_ew(prog, inputs, out=None, p: tf_params | None = None, stream=None):
     """Evaluate program ``prog`` (rows (op, dst, a, b)) over twofold inputs.
 
-    inputs: list of (hi, lo) CUDA float64 tensors, lo None for dotted input.
-    Returns (z0, z1, flags) tensors (or fills ``out``)."""
+    inputs: list of (hi, lo) CUDA float64 tensors, lo None for dotted input
+    (or pinned host tensors that the device maps: the kernel then reads and
+    writes host memory across the link).  Returns (z0, z1, flags) tensors
+    (or fills ``out``)."""
     pa = _prog_array(prog)
     n = inputs[0][0].numel()
-    ins = (tf_in * len(inputs))(*[tf_in(_dev(h, "hi"), _dev(lo, "lo")) for h, lo in inputs])
+    ins = (tf_in * len(inputs))(*[tf_in(_dev(h, "hi", True), _dev(lo, "lo", True)) for h, lo in inputs])
     for h, lo in inputs:
         if h.numel() != n or (lo is not None and lo.numel() != n):
             raise ValueError("inputs must all have the same length")
     hi, lo_, fl = _outputs(n, inputs[0][0].device, out)
-    o = tf_out(_dev(hi), _dev(lo_), _dev(fl))
+    o = tf_out(_dev(hi, "out hi", True), _dev(lo_, "out lo", True), _dev(fl, "flags", True))
     _check(lib().twofold_ew(pa.ctypes.data, pa.shape[0], ins, len(inputs), n, o, _pp(p),
                             _stream(stream)), "twofold_ew")
     return hi, lo_, fl
@@ -189,9 +202,11 @@ def plain_ew(prog, his, out=None, stream=None):
     torch = _torch()
     pa = _prog_array(prog)
     n = his[0].numel()
-    ptrs = (ctypes.c_void_p * len(his))(*[_dev(h) for h in his])
-    out = torch.empty(n, dtype=torch.float64, device=his[0].device) if out is None else out
-    _check(lib().plain_ew(pa.ctypes.data, pa.shape[0], ptrs, len(his), n, _dev(out),
+    ptrs = (ctypes.c_void_p * len(his))(*[_dev(h, "input", True) for h in his])
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float64).pin_memory() if his[0].device.type == "cpu"
+               else torch.empty(n, dtype=torch.float64, device=his[0].device))
+    _check(lib().plain_ew(pa.ctypes.data, pa.shape[0], ptrs, len(his), n, _dev(out, "out", True),
                           _stream(stream)), "plain_ew")
     return out
 

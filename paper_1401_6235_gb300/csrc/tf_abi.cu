@@ -1,4 +1,4 @@
-// Status strings and version of the C ABI.
+// Status strings, version and the host-mapping query of the C ABI.
 #include "tf_host.cuh"
 
 extern "C" const char *twofold_strerror(int status) {
@@ -14,3 +14,13 @@ extern "C" const char *twofold_strerror(int status) {
 }
 
 extern "C" int twofold_version(void) { return 100; }
+
+extern "C" int twofold_host_mapped(const void *ptr) {
+    if (!ptr) return 0;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == ptr ? 1 : 0;
+}

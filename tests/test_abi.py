@@ -116,3 +116,13 @@ def test_horner_rejects_bad_degree(L):
     assert L.twofold_horner(FAKE, -1, FAKE, 10, out, None, None) == T.TF_EINVAL
     assert L.twofold_horner(FAKE, 5000, FAKE, 10, out, None, None) == T.TF_EINVAL
     assert L.twofold_horner(FAKE, 3, FAKE, 0, out, None, None) == T.TF_OK
+
+
+def test_host_mapped_query_without_device(L):
+    """The host-mapping query never fails: NULL and plain host memory (and
+    any pointer when no device is present) give 0."""
+    import numpy as np
+    assert L.twofold_host_mapped(None) == 0
+    a = np.zeros(16)
+    if not __import__("torch").cuda.is_available():
+        assert L.twofold_host_mapped(ctypes.c_void_p(a.ctypes.data)) == 0

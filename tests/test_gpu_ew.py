@@ -91,6 +91,33 @@ def test_chain_kernel_equals_interpreter():
         assert np.array_equal(host(u).view(np.uint8), host(v).view(np.uint8))
 
 
+def test_host_buffer_form_equals_device_buffers():
+    """Pinned host tensors that the device maps stand in for device buffers
+    (the kernels read and write them across the host link): the same bits
+    as device buffers and as the oracle; an unpinned host tensor is refused."""
+    import torch
+    n = 100003
+    d = synth.ew_chain(n, seed=5)
+    ins = [(d[k + "0"], d[k + "1"]) for k in "abcd"]
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    hins = [(pin(h), pin(lo)) for h, lo in ins]
+    assert T.lib().twofold_host_mapped(T.ctypes.c_void_p(hins[0][0].data_ptr())) == 1
+    dz = T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, [(dev(h), dev(lo)) for h, lo in ins])
+    hz = T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, hins)
+    torch.cuda.synchronize()
+    assert all(not t.is_cuda and t.is_pinned() for t in hz)
+    for u, v in zip(dz, hz):
+        assert np.array_equal(host(u).view(np.uint8), v.numpy().view(np.uint8))
+    r0, r1, rf = O.ew(T.CHAIN_SQRT_MAD_DIV, ins)
+    assert_bits(hz[0].numpy(), r0, "host z0")
+    assert_bits(hz[1].numpy(), r1, "host z1")
+    pz = T.plain_ew(T.CHAIN_SQRT_MAD_DIV, [h for h, _ in hins])
+    torch.cuda.synchronize()
+    assert_bits(pz.numpy(), r0, "host plain == z0")
+    with pytest.raises(ValueError):
+        T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, [(torch.from_numpy(h), None) for h, _ in ins])
+
+
 @pytest.mark.parametrize("mode", [T.PANIC_REL, T.PANIC_ULP])
 def test_chain_flag_modes(mode):
     n = 50001
