@@ -47,6 +47,15 @@ HORNER_BYTES = 8 + 16 + 1                # x in, twofold out, flag
 HORNER_OPS_PER_STEP = 4 + 7              # MTF1.1 + ATF1.1
 
 
+# DRAM bytes per launch of the timed kernel from one ncu capture (summaries in
+# profiles/), scaled by the units a launch processes; None where the kernel
+# changed after its counters were taken.
+TRAFFIC_PER_UNIT = {
+    "ew_chain": (20.63e9 / (1 << 28), "profiles/chain_kernel_ew_chain_n2e28.md"),
+    "horner": (1.571e9 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
+}
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -207,7 +216,7 @@ def workload_ew(args, rank, world, dist_on):
                 "h2d_bytes_per_step": 64 * n, "d2h_bytes_per_step": 17 * n},
         "gpu_launches": args.steps,
         "clocks": cs.summary(),
-        "_kernel_ms": per, "_ops": EW_OPS * n, "_bytes": EW_BYTES * n,
+        "_kernel_ms": per, "_ops": EW_OPS * n, "_bytes": EW_BYTES * n, "_units": n,
         "_sample": lambda: cpu_sample_ew(n),
     }
     return res
@@ -265,7 +274,7 @@ def workload_dot(args, rank, world, dist_on):
         "e2e": {"value": e2e_ms / args.steps * 1e3, "unit": "us", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 16},
         "gpu_launches": 2 * args.steps, "clocks": cs.summary(),    # leaves kernel + final tree
-        "_kernel_ms": per, "_ops": DOT_OPS * n, "_bytes": DOT_BYTES * n,
+        "_kernel_ms": per, "_ops": DOT_OPS * n, "_bytes": DOT_BYTES * n, "_units": n,
         "_sample": lambda: cpu_sample_dot(n),
     }
 
@@ -308,7 +317,8 @@ def workload_cond_dots(args, rank, world, dist_on):
         "config": {"workload": f"{nj} ill-conditioned dots x 2^16, cond 10^U(2,30)", "n": nj * n,
                    "l2": f"inputs ({nj * n * 16 / 2**30:g} GiB) larger than L2", "parallelism": f"replicas x{world}"},
         "gpu_launches": args.steps, "clocks": cs.summary(),
-        "_kernel_ms": per, "_ops": DOT_OPS * nj * n, "_bytes": DOT_BYTES * nj * n, "_sample": None,
+        "_kernel_ms": per, "_ops": DOT_OPS * nj * n, "_bytes": DOT_BYTES * nj * n, "_units": nj * n,
+        "_sample": None,
     }
 
 
@@ -342,7 +352,7 @@ def workload_horner(args, rank, world, dist_on):
                    "n": int(x.size), "l2": "inputs 512 MiB larger than L2", "parallelism": f"replicas x{world}"},
         "gpu_launches": args.steps, "clocks": cs.summary(),
         "_kernel_ms": per, "_ops": HORNER_OPS_PER_STEP * steps_total + len(ks) * npts,
-        "_bytes": HORNER_BYTES * x.size, "_sample": None,
+        "_bytes": HORNER_BYTES * x.size, "_units": x.size, "_sample": None,
     }
 
 
@@ -420,6 +430,9 @@ def main():
     res = WORKLOADS[args.workload](args, rank, world, dist_on)
     sample = res.pop("_sample")
     kms, ops, nbytes = res.pop("_kernel_ms"), res.pop("_ops"), res.pop("_bytes")
+    units = res.pop("_units", None)
+    tr = TRAFFIC_PER_UNIT.get(args.workload)
+    traffic = round(tr[0] * units) if tr and units else None
     if rank == 0:
         hbm, src = measured_peaks()
         clk = res["clocks"]["sm_mhz"] or 2070.0
@@ -427,7 +440,8 @@ def main():
         peak_fp64 = FP64_OPS_PER_CLK_SM * sms * clk * 1e6 / 1e12
         achieved = ops / (kms * 1e-3) / 1e12
         res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                           "frac": achieved / peak_fp64, "traffic": None,
+                           "frac": achieved / peak_fp64, "traffic": traffic,
+                           "traffic_source": tr[1] if traffic else None,
                            "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
                                    f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
         res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
