@@ -248,6 +248,73 @@ int plain_horner_batched(const double *coefs, const int32_t *coef_offs, const in
                          int32_t njobs, const double *x, const int64_t *x_offs, double *out,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* ----------------------------------------------- mixed persistent batches
+ *
+ * Sum, dot and Horner jobs of any number and sizes in ONE persistent launch.
+ * No paper counterpart (a GPU interface): every job's result is the result
+ * of its single-job entry point (twofold_sum, twofold_dot, twofold_horner
+ * with the same tf_params), bit for bit, whatever the mix and the config.
+ *
+ * Work items are an aligned block of B = cfg->leaves_per_item leaves of a
+ * sum/dot job, or a range of cfg->points_per_item points of a Horner job.
+ * A job of more than B leaves is split into several items; since an aligned
+ * block of 2^k leaves is a subtree of the blocked pairwise order (see
+ * twofold_sum), the CTA that completes the job's last item combines the
+ * item partials with the same tree.  Resident CTAs take items largest first
+ * from an atomic counter; no CTA ever waits for another.
+ *
+ * twofold_batch_prepare validates the jobs (as the single-job calls do),
+ * builds the job and item tables and zeroes the counters in `ws`
+ * (ws_bytes >= twofold_batch_workspace_bytes(...), 256-byte aligned) with
+ * stream-ordered copies from host memory (it may wait for earlier work on
+ * `stream`), and fills `plan`.  twofold_batch_launch starts the persistent
+ * kernel of a prepared plan: it does no host work besides the launch, so it
+ * may be captured into a CUDA graph and replayed; the kernel leaves the
+ * counters zeroed for the next launch.  Launches of one plan must not
+ * overlap (one stream), and the plan's workspace and the jobs' buffers must
+ * stay valid.  twofold_batch = prepare + launch.
+ *
+ * Jobs: tf_job.kind TF_JOB_SUM / TF_JOB_DOT: x (and y) as in twofold_sum /
+ * twofold_dot, one result at out.hi[0], out.lo[0] (out.flags[0] if
+ * non-NULL); n == 0 gives (+0, +0).  TF_JOB_HORNER: degree k in
+ * [0, TF_HORNER_MAX_K], coefs (k+1 ascending, device), points x.hi (x.lo
+ * NULL), n results in out.  All pointers device pointers.
+ * Config (NULL: defaults): leaves_per_item a power of two in [1, threads]
+ * (256), points_per_item >= 1 (16384), threads 128 / 256 / 512 (256),
+ * ctas_per_sm >= 0 (0: by occupancy).  Errors: TF_EINVAL (bad job, config
+ * or plan), TF_ENOSPC (workspace too small or not 256-byte aligned),
+ * TF_EUNSUPPORTED (more than 2^31 - 1
+ * items), TF_ECUDA. */
+enum { TF_JOB_SUM = 1, TF_JOB_DOT = 2, TF_JOB_HORNER = 3 };
+
+typedef struct {
+    int32_t kind;          /* TF_JOB_SUM, TF_JOB_DOT or TF_JOB_HORNER            */
+    int32_t k;             /* Horner degree                                      */
+    int64_t n;             /* elements (sum, dot) or points (Horner), >= 0       */
+    tf_in x;               /* operand / Horner points in x.hi                    */
+    tf_in y;               /* dot: second operand                                */
+    const double *coefs;   /* Horner coefficients                                */
+    tf_out out;            /* results                                            */
+} tf_job;
+
+typedef struct {
+    int32_t leaves_per_item;
+    int32_t points_per_item;
+    int32_t threads;
+    int32_t ctas_per_sm;
+} tf_batch_config;
+
+typedef struct { int64_t opaque[16]; } tf_batch_plan;   /* filled by twofold_batch_prepare */
+
+size_t twofold_batch_workspace_bytes(const tf_job *jobs, int32_t njobs, const tf_params *p,
+                                     const tf_batch_config *cfg);   /* 0 for an invalid list */
+int twofold_batch_prepare(const tf_job *jobs, int32_t njobs, const tf_params *p,
+                          const tf_batch_config *cfg, void *ws, size_t ws_bytes, tf_batch_plan *plan,
+                          void *stream);
+int twofold_batch_launch(const tf_batch_plan *plan, void *stream);
+int twofold_batch(const tf_job *jobs, int32_t njobs, const tf_params *p, const tf_batch_config *cfg,
+                  void *ws, size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

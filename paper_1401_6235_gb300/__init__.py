@@ -50,6 +50,23 @@ class tf_params(ctypes.Structure):
                 ("panic_tau", ctypes.c_double), ("panic_ulps", ctypes.c_double)]
 
 
+class tf_job(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("n", ctypes.c_int64), ("x", tf_in),
+                ("y", tf_in), ("coefs", ctypes.c_void_p), ("out", tf_out)]
+
+
+class tf_batch_config(ctypes.Structure):
+    _fields_ = [("leaves_per_item", ctypes.c_int32), ("points_per_item", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+class tf_batch_plan(ctypes.Structure):
+    _fields_ = [("opaque", ctypes.c_int64 * 16)]
+
+
+JOB_SUM, JOB_DOT, JOB_HORNER = 1, 2, 3
+
+
 def params(panic_mode: int = PANIC_REL, leaf: int = 256, panic_tau: float = 2.0 ** -40,
            panic_ulps: float = 4096.0) -> tf_params:
     return tf_params(panic_mode, leaf, panic_tau, panic_ulps)
@@ -78,6 +95,11 @@ SIGNATURES = {
     "twofold_horner_batched": ([_P, _P, _P, _I32, _P, _P, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
     "plain_horner": ([_P, _I32, _P, _I64, _P, _P], ctypes.c_int),
     "plain_horner_batched": ([_P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+    "twofold_batch_workspace_bytes": ([_P, _I32, _PP, ctypes.POINTER(tf_batch_config)], _SZ),
+    "twofold_batch_prepare": ([_P, _I32, _PP, ctypes.POINTER(tf_batch_config), _P, _SZ,
+                               ctypes.POINTER(tf_batch_plan), _P], ctypes.c_int),
+    "twofold_batch_launch": ([ctypes.POINTER(tf_batch_plan), _P], ctypes.c_int),
+    "twofold_batch": ([_P, _I32, _PP, ctypes.POINTER(tf_batch_config), _P, _SZ, _P], ctypes.c_int),
 }
 
 _lib = None

@@ -126,3 +126,35 @@ def test_host_mapped_query_without_device(L):
     a = np.zeros(16)
     if not __import__("torch").cuda.is_available():
         assert L.twofold_host_mapped(ctypes.c_void_p(a.ctypes.data)) == 0
+
+
+def test_batch_rejects_bad_jobs_and_configs(L):
+    """Host-side checks of the mixed batch, before any device call."""
+    J = T.tf_job * 2
+    out = T.tf_out(FAKE, FAKE, None)
+    good = J(T.tf_job(T.JOB_DOT, 0, 100, T.tf_in(FAKE, None), T.tf_in(FAKE, None), None, out),
+             T.tf_job(T.JOB_HORNER, 5, 100, T.tf_in(FAKE, None), T.tf_in(None, None), FAKE, out))
+    cfg = lambda *a: ctypes.byref(T.tf_batch_config(*a))
+    plan = T.tf_batch_plan()
+    assert L.twofold_batch_workspace_bytes(good, 2, None, None) > 0
+    for c in [(3, 4096, 256, 0), (512, 4096, 256, 0), (32, 0, 256, 0), (32, 4096, 100, 0), (32, 4096, 256, -1)]:
+        assert L.twofold_batch_workspace_bytes(good, 2, None, cfg(*c)) == 0, c
+        assert L.twofold_batch_prepare(good, 2, None, cfg(*c), FAKE, 1 << 30, ctypes.byref(plan), None) == T.TF_EINVAL
+    bad = J(*good)
+    bad[0].kind = 9
+    assert L.twofold_batch_prepare(bad, 2, None, None, FAKE, 1 << 30, ctypes.byref(plan), None) == T.TF_EINVAL
+    bad = J(*good)
+    bad[1].x = T.tf_in(FAKE, FAKE)                  # Horner points take no tails
+    assert L.twofold_batch_prepare(bad, 2, None, None, FAKE, 1 << 30, ctypes.byref(plan), None) == T.TF_EINVAL
+    bad = J(*good)
+    bad[1].k = 5000
+    assert L.twofold_batch_prepare(bad, 2, None, None, FAKE, 1 << 30, ctypes.byref(plan), None) == T.TF_EINVAL
+    bad = J(*good)
+    bad[0].x = T.tf_in(FAKE + 4, None)              # misaligned
+    assert L.twofold_batch_prepare(bad, 2, None, None, FAKE, 1 << 30, ctypes.byref(plan), None) == T.TF_EINVAL
+    bad = J(*good)
+    bad[0].n = -1
+    assert L.twofold_batch_prepare(bad, 2, None, None, FAKE, 1 << 30, ctypes.byref(plan), None) == T.TF_EINVAL
+    assert L.twofold_batch_prepare(good, 2, None, None, FAKE, 64, ctypes.byref(plan), None) == T.TF_ENOSPC
+    assert L.twofold_batch_prepare(good, 2, None, None, FAKE + 8, 1 << 30, ctypes.byref(plan), None) == T.TF_ENOSPC
+    assert L.twofold_batch_launch(ctypes.byref(T.tf_batch_plan()), None) == T.TF_EINVAL   # not prepared
