@@ -356,8 +356,88 @@ def workload_horner(args, rank, world, dist_on):
     }
 
 
+def workload_batch_mix(args, rank, world, dist_on):
+    """Thousands of uneven sum / dot / Horner jobs: one persistent launch of
+    the mixed batch (replayed from a CUDA graph, configuration chosen by the
+    autotuner) against one entry-point call per job, on the same data, with
+    the results compared bit for bit."""
+    import torch
+    import paper_1401_6235_gb300 as T
+    from paper_1401_6235_gb300 import batch as B
+    import synth
+    rng = np.random.default_rng(1000 + rank)
+    nj = args.n or 2000
+    kinds = rng.choice([T.JOB_DOT, T.JOB_SUM, T.JOB_HORNER], size=nj, p=[0.5, 0.25, 0.25])
+    sizes = np.floor(10.0 ** rng.uniform(3, 6, nj)).astype(np.int64)
+    degs = rng.integers(8, 31, nj)
+    red = kinds != T.JOB_HORNER
+    n_red, n_h = int(sizes[red].sum()), int(sizes[~red].sum())
+    x, y = synth.dot_uniform(n_red, seed=rank)
+    pts = synth.horner_points(n_h, seed=rank, stream=7)
+    gx, gy, gp = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(pts).cuda()
+    coef = {k: torch.from_numpy(synth.binomial_coefs(k)).cuda() for k in range(8, 31)}
+    jobs, a, b = [], 0, 0
+    for kind, n, k in zip(kinds, sizes, degs):
+        n = int(n)
+        if kind == T.JOB_HORNER:
+            jobs.append(B.horner_job(coef[int(k)], gp[b:b + n]))
+            b += n
+        elif kind == T.JOB_DOT:
+            jobs.append(B.dot_job(gx[a:a + n], gy[a:a + n]))
+            a += n
+        else:
+            jobs.append(B.sum_job(gx[a:a + n]))
+            a += n
+    cands = [(32, 4096, 128), (64, 16384, 256), (256, 16384, 256), (256, 4096, 256), (128, 65536, 512),
+             (512, 65536, 512)]
+    cfg = B.tune(jobs, cands=cands, reps=3)
+    batch = B.Batch(jobs, cfg=cfg)
+    g = batch.graph()
+    with ClockSampler(args.smi_index) as cs:
+        ms = time_steps(g.replay, args.steps, args.warmup, dist_on)
+    got = [tuple(t.clone() for t in j.out) for j in jobs]
+    # the same jobs, one entry-point call each (workspaces allocated up front)
+    wsz = max(T.lib().twofold_workspace_bytes(T.KIND_DOT, int(n), 1, None) for n in sizes)
+    ws = T.workspace(max(wsz, 256))
+
+    def per_job():
+        for j in jobs:
+            if j.kind == T.JOB_DOT:
+                T.twofold_dot(j.x, j.y, out=j.out, ws=ws)
+            elif j.kind == T.JOB_SUM:
+                T.twofold_sum(j.x, out=j.out, ws=ws)
+            else:
+                T.twofold_horner(j.coefs, j.x, out=j.out)
+
+    pj_ms = time_steps(per_job, max(3, args.steps // 4), args.warmup, dist_on)
+    torch.cuda.synchronize()
+    same = all(torch.equal(u.view(torch.uint8), v.view(torch.uint8)) for o, j in zip(got, jobs)
+               for u, v in zip(o, j.out))
+    per = ms / args.steps
+    pj = pj_ms / max(3, args.steps // 4)
+    n_dot = int(sizes[kinds == T.JOB_DOT].sum())
+    n_sum = n_red - n_dot
+    hsteps = int((sizes[~red] * degs[~red]).sum())
+    return {
+        "metric": f"mixed batch jobs/s ({nj} jobs: dot 50%, sum 25%, Horner k 8-30 25%; sizes 10^U(3,6))",
+        "value": nj * world / (per * 1e-3), "unit": "jobs/s", "ms_per_step": per,
+        "per_job_launches": {"value": nj * world / (pj * 1e-3), "unit": "jobs/s", "ms_per_step": pj,
+                             "launches_per_step": int(nj + (kinds != T.JOB_HORNER).sum())},
+        "speedup_vs_per_job": pj / per, "same_bits_as_per_job": bool(same),
+        "tuned_config": {"leaves_per_item": cfg.leaves_per_item, "points_per_item": cfg.points_per_item,
+                         "threads": cfg.threads},
+        "config": {"workload": "mixed sum/dot/Horner batch, x,y ~ U[-1,1], Horner x ~ U[0.9,1.1], binomial "
+                               "coefficients", "jobs": nj, "elements": n_red, "points": n_h,
+                   "l2": f"inputs ({(16 * n_red + 8 * n_h) / 2**30:.1f} GiB) larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": args.steps, "clocks": cs.summary(),
+        "_kernel_ms": per, "_ops": DOT_OPS * n_dot + 8 * n_sum + HORNER_OPS_PER_STEP * hsteps,
+        "_bytes": DOT_BYTES * n_dot + 8 * n_sum + HORNER_BYTES * n_h, "_units": nj, "_sample": None,
+    }
+
+
 WORKLOADS = {"ew_chain": workload_ew, "dot": workload_dot, "cond_dots": workload_cond_dots,
-             "horner": workload_horner}
+             "horner": workload_horner, "batch_mix": workload_batch_mix}
 
 
 # -------------------------------------------------------------- reference
