@@ -15,7 +15,8 @@
  *    algorithms (see twofold_ew for the exact rule).
  *  - Unless stated otherwise, data pointers are DEVICE pointers owned by the
  *    caller (for example torch tensors); the library never allocates, frees
- *    or synchronises.  Every call is asynchronous on `stream` (a
+ *    or synchronises (the request server below is the one exception: it owns
+ *    a device arena and a scheduler thread).  Every call is asynchronous on `stream` (a
  *    cudaStream_t passed as void*; NULL is the legacy default stream).
  *  - Pinned host memory that the device maps at the same address (memory
  *    from cudaHostAlloc / cudaMallocHost under unified addressing;
@@ -314,6 +315,78 @@ int twofold_batch_prepare(const tf_job *jobs, int32_t njobs, const tf_params *p,
 int twofold_batch_launch(const tf_batch_plan *plan, void *stream);
 int twofold_batch(const tf_job *jobs, int32_t njobs, const tf_params *p, const tf_batch_config *cfg,
                   void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------ serving loop
+ *
+ * A request server (no paper counterpart: a serving interface over the
+ * entry points above).  twofold_server_create reserves a device arena of
+ * mem_cap_bytes (the only entry point that allocates device memory) and
+ * starts one scheduler thread.  Requests carry HOST buffers; they wait in
+ * FIFO order, and whenever memory and a stream are free the scheduler admits
+ * the longest prefix of the queue that fits the arena (inputs, outputs and
+ * the batch workspace), up to max_batch_jobs requests, copies the inputs in,
+ * runs the sum / dot / Horner requests as one mixed persistent batch
+ * (twofold_batch, with `cfg`) and the elementwise requests as twofold_ew
+ * launches, copies the results out and releases the memory when the batch's
+ * event fires.  Up to three batches are in flight on a pool of streams, so
+ * requests that arrive while others run are admitted as memory frees up and
+ * their copies and kernels overlap.  A request's results are those of the
+ * single-job entry point on the same inputs (the same bits), alone or in any
+ * mix.  A request larger than the whole arena fails with TF_ENOSPC.
+ *
+ * Requests (tf_request): kind TF_JOB_SUM (in[0] = x, in[1] = x tails or
+ * NULL), TF_JOB_DOT (in[0..3] = x, x tails, y, y tails; tails may be NULL),
+ * TF_JOB_HORNER (in[0] = points, coefs = k+1 coefficients), TF_JOB_EW
+ * (program prog/nprog as for twofold_ew over nin <= 4 twofold inputs,
+ * in[2i] = hi, in[2i+1] = lo or NULL; the program is copied at submit).
+ * Outputs: out_hi, out_lo (1 result for sum/dot, n for Horner and
+ * elementwise), out_flags optional.  All in/out pointers are HOST pointers
+ * that must stay valid until twofold_server_wait returns for the ticket;
+ * page-locked outputs let the copies run asynchronously (pageable ones make
+ * the scheduler wait for them).  Every ticket must be waited for once.
+ *
+ * twofold_server_wait blocks until the request is done (timeout_ms < 0:
+ * without limit) and returns its status (TF_ETIMEOUT when the time ran out;
+ * the ticket stays valid), filling `info` with host clock stamps
+ * (steady clock, ns) of submission, admission and completion and the size
+ * of the batch the request ran in.  twofold_server_destroy finishes every
+ * pending request, stops the thread and frees the arena. */
+enum { TF_JOB_EW = 4 };
+
+typedef struct tf_server tf_server;
+
+typedef struct {
+    int32_t kind;
+    int32_t k;                 /* Horner degree                              */
+    int64_t n;                 /* elements / points                          */
+    const double *in[8];       /* host inputs, see above                     */
+    const double *coefs;       /* Horner coefficients (host)                 */
+    const int32_t *prog;       /* elementwise program (host, nprog rows of 4) */
+    int32_t nprog;
+    int32_t nin;               /* elementwise twofold inputs (1..4)          */
+    double *out_hi;            /* host outputs                               */
+    double *out_lo;
+    uint8_t *out_flags;
+} tf_request;
+
+typedef struct {
+    int64_t submitted_ns, admitted_ns, done_ns;
+    int32_t status;            /* TF_OK or a negative tf_status              */
+    int32_t batch_jobs;        /* requests in the batch it ran in            */
+} tf_request_info;
+
+typedef struct {
+    int64_t completed, failed, batches, batched_jobs;
+    int64_t arena_bytes, peak_bytes, pending;
+    int32_t max_inflight, inflight;
+} tf_server_stats;
+
+int twofold_server_create(size_t mem_cap_bytes, int32_t max_batch_jobs, const tf_params *p,
+                          const tf_batch_config *cfg, tf_server **out);
+int twofold_server_submit(tf_server *s, const tf_request *r, uint64_t *ticket);
+int twofold_server_wait(tf_server *s, uint64_t ticket, int32_t timeout_ms, tf_request_info *info);
+int twofold_server_stats(tf_server *s, tf_server_stats *out);
+int twofold_server_destroy(tf_server *s);
 
 #ifdef __cplusplus
 }

@@ -64,7 +64,25 @@ class tf_batch_plan(ctypes.Structure):
     _fields_ = [("opaque", ctypes.c_int64 * 16)]
 
 
-JOB_SUM, JOB_DOT, JOB_HORNER = 1, 2, 3
+class tf_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("inp", ctypes.c_void_p * 8), ("coefs", ctypes.c_void_p), ("prog", ctypes.c_void_p),
+                ("nprog", ctypes.c_int32), ("nin", ctypes.c_int32), ("out_hi", ctypes.c_void_p),
+                ("out_lo", ctypes.c_void_p), ("out_flags", ctypes.c_void_p)]
+
+
+class tf_request_info(ctypes.Structure):
+    _fields_ = [("submitted_ns", ctypes.c_int64), ("admitted_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("batch_jobs", ctypes.c_int32)]
+
+
+class tf_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("batched_jobs", ctypes.c_int64), ("arena_bytes", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("max_inflight", ctypes.c_int32), ("inflight", ctypes.c_int32)]
+
+
+JOB_SUM, JOB_DOT, JOB_HORNER, JOB_EW = 1, 2, 3, 4
 
 
 def params(panic_mode: int = PANIC_REL, leaf: int = 256, panic_tau: float = 2.0 ** -40,
@@ -100,6 +118,11 @@ SIGNATURES = {
                                ctypes.POINTER(tf_batch_plan), _P], ctypes.c_int),
     "twofold_batch_launch": ([ctypes.POINTER(tf_batch_plan), _P], ctypes.c_int),
     "twofold_batch": ([_P, _I32, _PP, ctypes.POINTER(tf_batch_config), _P, _SZ, _P], ctypes.c_int),
+    "twofold_server_create": ([_SZ, _I32, _PP, ctypes.POINTER(tf_batch_config), ctypes.POINTER(_P)], ctypes.c_int),
+    "twofold_server_submit": ([_P, ctypes.POINTER(tf_request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "twofold_server_wait": ([_P, ctypes.c_uint64, _I32, ctypes.POINTER(tf_request_info)], ctypes.c_int),
+    "twofold_server_stats": ([_P, ctypes.POINTER(tf_server_stats)], ctypes.c_int),
+    "twofold_server_destroy": ([_P], ctypes.c_int),
 }
 
 _lib = None

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-fmad=false", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
               "-Xptxas", "-v"]
-SOURCES = ["tf_abi.cu", "tf_ew.cu", "tf_reduce.cu", "tf_horner.cu", "tf_batch.cu"]
+SOURCES = ["tf_abi.cu", "tf_ew.cu", "tf_reduce.cu", "tf_horner.cu", "tf_batch.cu", "tf_serve.cu"]
 
 
 def nvcc() -> str:

@@ -158,3 +158,20 @@ def test_batch_rejects_bad_jobs_and_configs(L):
     assert L.twofold_batch_prepare(good, 2, None, None, FAKE, 64, ctypes.byref(plan), None) == T.TF_ENOSPC
     assert L.twofold_batch_prepare(good, 2, None, None, FAKE + 8, 1 << 30, ctypes.byref(plan), None) == T.TF_ENOSPC
     assert L.twofold_batch_launch(ctypes.byref(T.tf_batch_plan()), None) == T.TF_EINVAL   # not prepared
+
+
+def test_server_rejects_bad_arguments(L):
+    """Host-side checks of the request server (no device needed)."""
+    h = ctypes.c_void_p()
+    assert L.twofold_server_create(100, 16, None, None, ctypes.byref(h)) == T.TF_EINVAL      # arena too small
+    assert L.twofold_server_create(1 << 20, 0, None, None, ctypes.byref(h)) == T.TF_EINVAL   # no batch slots
+    bad = T.params(leaf=0)
+    assert L.twofold_server_create(1 << 20, 16, ctypes.byref(bad), None, ctypes.byref(h)) == T.TF_EINVAL
+    cfg = T.tf_batch_config(3, 4096, 256, 0)
+    assert L.twofold_server_create(1 << 20, 16, None, ctypes.byref(cfg), ctypes.byref(h)) == T.TF_EINVAL
+    assert L.twofold_server_create(1 << 20, 16, None, None, None) == T.TF_EINVAL
+    r = T.tf_request()
+    tid = ctypes.c_uint64()
+    assert L.twofold_server_submit(None, ctypes.byref(r), ctypes.byref(tid)) == T.TF_EINVAL
+    assert L.twofold_server_wait(None, 1, 0, None) == T.TF_EINVAL
+    assert L.twofold_server_destroy(None) == T.TF_EINVAL
