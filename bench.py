@@ -436,8 +436,150 @@ def workload_batch_mix(args, rank, world, dist_on):
     }
 
 
+def workload_serve(args, rank, world, dist_on):
+    """A Poisson stream of mixed requests (dot 40 %, sum 20 %, Horner k 8-30
+    20 %, elementwise chain 20 %; sizes 10^U(3,6)) through the request server
+    at several arrival rates: achieved jobs/s and p50 / p99 latency from
+    submission to completion, against a one-worker server that runs each
+    request alone (copy in, single-job call, copy out, synchronise) on the
+    same arrival times (its queue is replayed from measured service times)."""
+    import torch
+    import paper_1401_6235_gb300 as T
+    from paper_1401_6235_gb300.serve import Server
+    import synth
+    rng = np.random.default_rng(2000 + rank)
+    nreq = args.n or 3000
+    rates = [4000.0, 16000.0, 64000.0]
+    pool = 1 << 21
+    pin = lambda m: torch.empty(m, dtype=torch.float64).pin_memory().numpy()
+    xy = synth.ew_chain(pool, seed=rank, pinned=pin)              # 8 pinned pools of 2^21 doubles
+    hx = synth.horner_points(pool, seed=rank, stream=5)
+    coef = {k: synth.binomial_coefs(k) for k in range(8, 31)}
+    kinds = rng.choice(["dot", "sum", "horner", "ew"], size=nreq, p=[0.4, 0.2, 0.2, 0.2])
+    sizes = np.floor(10.0 ** rng.uniform(3, 6, nreq)).astype(np.int64)
+    offs = (rng.random(nreq) * (pool - sizes)).astype(np.int64)
+    degs = rng.integers(8, 31, nreq)
+
+    def args_of(i):
+        a, n = int(offs[i]), int(sizes[i])
+        sl = slice(a, a + n)
+        if kinds[i] == "dot":
+            return ("dot", xy["a0"][sl], xy["b0"][sl])
+        if kinds[i] == "sum":
+            return ("sum", xy["c0"][sl])
+        if kinds[i] == "horner":
+            return ("horner", coef[int(degs[i])], hx[sl])
+        return ("ew", [(xy[c + "0"][sl], xy[c + "1"][sl]) for c in "abcd"])
+
+    reqs = [args_of(i) for i in range(nreq)]
+    # requests built up front (ctypes structs, outputs in shared pinned scratch: the
+    # timed loop only submits), so that the client can offer rates above the server's
+    import ctypes
+    prog = np.ascontiguousarray(np.asarray(T.CHAIN_SQRT_MAD_DIV, np.int32))
+    oh, ol = pin(pool), pin(pool)
+    of = torch.empty(pool, dtype=torch.uint8).pin_memory().numpy()
+    kind_id = {"dot": T.JOB_DOT, "sum": T.JOB_SUM, "horner": T.JOB_HORNER, "ew": T.JOB_EW}
+    structs = []
+    for r in reqs:
+        q = T.tf_request()
+        q.kind = kind_id[r[0]]
+        if r[0] == "dot":
+            q.n, q.inp[0], q.inp[2] = r[1].size, r[1].ctypes.data, r[2].ctypes.data
+        elif r[0] == "sum":
+            q.n, q.inp[0] = r[1].size, r[1].ctypes.data
+        elif r[0] == "horner":
+            q.n, q.k, q.coefs, q.inp[0] = r[2].size, r[1].size - 1, r[1].ctypes.data, r[2].ctypes.data
+        else:
+            q.n = r[1][0][0].size
+            for i, (h, lo) in enumerate(r[1]):
+                q.inp[2 * i], q.inp[2 * i + 1] = h.ctypes.data, lo.ctypes.data
+            q.prog, q.nprog, q.nin = prog.ctypes.data, prog.shape[0], 4
+        q.out_hi, q.out_lo, q.out_flags = oh.ctypes.data, ol.ctypes.data, of.ctypes.data
+        structs.append(q)
+    L = T.lib()
+    submit_c, wait_c = L.twofold_server_submit, L.twofold_server_wait
+
+    sweep, arrivals = [], []
+    with Server(mem_cap=32 << 30, max_batch_jobs=4096) as srv:
+        h = srv._h
+        tid = ctypes.c_uint64()
+        info = T.tf_request_info()
+        for q in structs[:50]:                       # warm the server, the allocator and the kernels
+            submit_c(h, ctypes.byref(q), ctypes.byref(tid))
+            wait_c(h, tid.value, -1, ctypes.byref(info))
+        for rate in rates:
+            arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
+            arrivals.append(arrive)
+            ids = np.empty(nreq, np.uint64)
+            t0 = time.perf_counter()
+            for i, q in enumerate(structs):
+                while time.perf_counter() - t0 < arrive[i]:
+                    pass
+                st_ = submit_c(h, ctypes.byref(q), ctypes.byref(tid))
+                if st_ != 0:
+                    raise RuntimeError(f"submit: {T.strerror(st_)}")
+                ids[i] = tid.value
+            sub_s = time.perf_counter() - t0
+            rec = np.empty((nreq, 3))
+            for i in range(nreq):
+                if wait_c(h, int(ids[i]), -1, ctypes.byref(info)) != 0:
+                    raise RuntimeError("request failed")
+                rec[i] = (info.submitted_ns, info.done_ns, info.batch_jobs)
+            lat = (rec[:, 1] - rec[:, 0]) * 1e-6
+            span = (rec[:, 1].max() - rec[:, 0].min()) * 1e-9
+            sweep.append({"rate": rate, "offered_jobs_s": nreq / sub_s, "jobs_s": nreq / span,
+                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "mean_batch": float(rec[:, 2].mean())})
+        stats = srv.stats()
+
+    # one request at a time: copy in, single-job call, copy out, synchronise
+    ws = T.workspace(T.lib().twofold_workspace_bytes(T.KIND_DOT, pool, 1, None))
+    service = np.empty(nreq)
+    for i, r in enumerate(reqs):
+        t = time.perf_counter()
+        if r[0] == "dot":
+            o = T.twofold_dot(torch.from_numpy(r[1]).cuda(non_blocking=True),
+                              torch.from_numpy(r[2]).cuda(non_blocking=True), ws=ws)
+        elif r[0] == "sum":
+            o = T.twofold_sum(torch.from_numpy(r[1]).cuda(non_blocking=True), ws=ws)
+        elif r[0] == "horner":
+            o = T.twofold_horner(torch.from_numpy(r[1]).cuda(non_blocking=True),
+                                 torch.from_numpy(r[2]).cuda(non_blocking=True))
+        else:
+            o = T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, [(torch.from_numpy(h).cuda(non_blocking=True),
+                                                     torch.from_numpy(lo).cuda(non_blocking=True)) for h, lo in r[1]])
+        [t_.cpu() for t_ in o]
+        torch.cuda.synchronize()
+        service[i] = time.perf_counter() - t
+    for row, arrive in zip(sweep, arrivals):       # the per-job server on the same arrival times
+        done = np.empty(nreq)
+        free = 0.0
+        for i in range(nreq):
+            free = max(arrive[i], free) + service[i]
+            done[i] = free
+        lat = (done - arrive) * 1e3
+        row["per_job"] = {"jobs_s": nreq / (done[-1] - arrive[0]), "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99))}
+    top = sweep[-1]
+    moved = sum(16 * int(sizes[i]) if kinds[i] == "dot" else 8 * int(sizes[i]) if kinds[i] == "sum" else
+                25 * int(sizes[i]) if kinds[i] == "horner" else 81 * int(sizes[i]) for i in range(nreq))
+    return {
+        "metric": "served twofold jobs/s at the highest offered rate (Poisson, mixed kinds), p50/p99 latency",
+        "value": top["jobs_s"], "unit": "jobs/s", "ms_per_step": 1e3 / top["jobs_s"],
+        "sweep": sweep, "server": {k: stats[k] for k in ("batches", "batched_jobs", "peak_bytes", "max_inflight")},
+        "config": {"workload": f"{nreq} requests per rate: dot 40%, sum 20%, Horner k 8-30 20%, chain 20%; sizes "
+                               "10^U(3,6) (the 10^7 end of the stated range scaled down so that a run's host "
+                               "traffic stays within a minute); inputs slices of pinned host pools; memory cap 32 GiB",
+                   "rates": rates, "parallelism": f"replicas x{world}"},
+        "e2e": {"value": top["jobs_s"], "unit": "jobs/s", "h2d_bytes_per_step": int(moved / nreq),
+                "d2h_bytes_per_step": None},
+        "gpu_launches": None, "clocks": {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0},
+        "_kernel_ms": 1e3 / top["jobs_s"], "_ops": 0, "_bytes": moved / nreq, "_units": None, "_sample": None,
+    }
+
+
 WORKLOADS = {"ew_chain": workload_ew, "dot": workload_dot, "cond_dots": workload_cond_dots,
-             "horner": workload_horner, "batch_mix": workload_batch_mix}
+             "horner": workload_horner, "batch_mix": workload_batch_mix, "serve": workload_serve}
 
 
 # -------------------------------------------------------------- reference
@@ -519,11 +661,13 @@ def main():
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak_fp64 = FP64_OPS_PER_CLK_SM * sms * clk * 1e6 / 1e12
         achieved = ops / (kms * 1e-3) / 1e12
-        res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                           "frac": achieved / peak_fp64, "traffic": traffic,
-                           "traffic_source": tr[1] if traffic else None,
-                           "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
-                                   f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
+        if ops == 0:                                   # a serving line: no single kernel to place
+            achieved = None
+        res["roofline"] = None if achieved is None else {
+            "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+            "frac": achieved / peak_fp64, "traffic": traffic, "traffic_source": tr[1] if traffic else None,
+            "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
+                    f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
         res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
         if sample is not None and not args.no_cpu_baseline:
