@@ -30,6 +30,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 ADD, SUB, MUL, DIV, SQRT = 1, 2, 3, 4, 5
+PADD, PSUB, PMUL, PDIV, PSQRT = 6, 7, 8, 9, 10     # coupled (Dekker emulation) operations
 PANIC, NONFINITE = 1, 2
 REL, ULP = 0, 1
 DEFAULT_TAU = 2.0 ** -40
@@ -67,10 +68,10 @@ def load(path: str) -> ctypes.CDLL:
     L = ctypes.CDLL(path)
     d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
     pd = ctypes.POINTER(ctypes.c_double)
-    for name in ("tfo_two_sum", "tfo_two_diff", "tfo_two_prod", "tfo_div_rem"):
+    for name in ("tfo_two_sum", "tfo_two_diff", "tfo_two_prod", "tfo_div_rem", "tfo_fast_two_sum"):
         getattr(L, name).argtypes = [d, d, pd, pd]
     L.tfo_sqrt_rem.argtypes = [d, pd, pd]
-    for name in ("tfo_atf1", "tfo_stf1", "tfo_mtf1", "tfo_dtf1"):
+    for name in ("tfo_atf1", "tfo_stf1", "tfo_mtf1", "tfo_dtf1", "tfo_mpf1", "tfo_dpf1"):
         getattr(L, name).argtypes = [d, d, d, d]
         getattr(L, name).restype = _TF
     for name in ("tfo_atf11", "tfo_stf11", "tfo_mtf11", "tfo_dtf11"):
@@ -113,6 +114,11 @@ def two_sum(a, b):
     return _pair(lib().tfo_two_sum, a, b)
 
 
+def fast_two_sum(a, b):
+    """Algorithm 1.1 (three operations, exact when |a| >= |b|): a + b -> (s, t)."""
+    return _pair(lib().tfo_fast_two_sum, a, b)
+
+
 def two_diff(a, b):
     """Algorithm 2.2 (signs read as Shewchuk's): a - b -> (d, t)."""
     return _pair(lib().tfo_two_diff, a, b)
@@ -146,6 +152,8 @@ def mtf11(x0, x1, y0): return _tf(lib().tfo_mtf11(x0, x1, y0))
 def dtf1(x0, x1, y0, y1): return _tf(lib().tfo_dtf1(x0, x1, y0, y1))
 def dtf11(x0, x1, y0): return _tf(lib().tfo_dtf11(x0, x1, y0))
 def dtf111(x0, y0): return _tf(lib().tfo_dtf111(x0, y0))
+def mpf1(x0, x1, y0, y1): return _tf(lib().tfo_mpf1(x0, x1, y0, y1))
+def dpf1(x0, x1, y0, y1): return _tf(lib().tfo_dpf1(x0, x1, y0, y1))
 def rpf1(x0, x1): return _tf(lib().tfo_rpf1(x0, x1))
 def rpf11(x0): return _tf(lib().tfo_rpf11(x0))
 def rtf1(x0, x1): return _tf(lib().tfo_rtf1(x0, x1))

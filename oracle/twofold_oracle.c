@@ -39,6 +39,15 @@
  *  R9  Panic flag (idea: Motivation, Applications; threshold not in the
  *      paper): bit0 PANIC if |z1| > tau*|z0| (REL) or |z1| > m*ulp(z0) (ULP);
  *      bit1 NONFINITE if z0 or z1 is NaN or infinite.
+ *  R10 "Coupled" (Dekker emulation) operations, the paper's p-prefixed
+ *      functions: add/subtract use ATF/STF (no special coupled algorithm
+ *      exists), multiply MPF 1 (MTF 1.1 when y is dotted), divide DPF 1
+ *      (DTF 1.1 when y is dotted), root RPF 1; the output is then
+ *      renormalised with Fast Two-Sum (Algorithm 1.1, its three operations
+ *      taken literally; Dekker arithmetic section, Applications).  With every
+ *      operand dotted the output of the exact transform / DTF 1.1.1 / RPF 1.1
+ *      is already coupled and is returned as is (Applications; the pdiv of
+ *      two dotted numbers in Fragment 4 returns tdiv unchanged).
  */
 #include <math.h>
 #include <stdint.h>
@@ -92,6 +101,16 @@ void tfo_sqrt_rem(double a, double *c, double *d) {
     double c_ = sqrt(a);
     *c = c_;
     *d = fma(-c_, c_, a);
+}
+
+/* Algorithm 1.1 (Fast Two-Sum): a + b -> s + t, exact when |a| >= |b|.
+ * Used to renormalise a twofold (Dekker arithmetic section), three
+ * operations taken literally whatever the magnitudes. */
+void tfo_fast_two_sum(double a, double b, double *s, double *t) {
+    double s_ = a + b;          /* (1) s  = a (+) b   */
+    double b1 = s_ - a;         /* (2) b' = s (-) a   */
+    *s = s_;
+    *t = b - b1;                /* (3) t  = b (-) b'  */
 }
 
 /* =========================================================== Algorithms */
@@ -200,6 +219,33 @@ tfo_tf tfo_dtf1(double x0, double x1, double y0, double y1) {
     return z;
 }
 
+/* MPF1 (coupled x, y): x_i * y_j -> p_ij + e_ij; z0 = p00;
+ *       z1 = e00 (+) (p01 (+) p10)   (p11 omitted: minor for coupled input). */
+tfo_tf tfo_mpf1(double x0, double x1, double y0, double y1) {
+    tfo_tf z;
+    double p00, e00;
+    tfo_two_prod(x0, y0, &p00, &e00);
+    double p01 = x0 * y1;
+    double p10 = x1 * y0;
+    double v = p01 + p10;
+    z.z0 = p00;
+    z.z1 = e00 + v;
+    return z;
+}
+
+/* DPF1 (coupled x, y): z0 = fl(x0/y0); r0 = fma(x0 - z0 y0); r1 = fma(x1 - z0 y1);
+ *       c0 = r0 (+) r1; z1 = fl(c0/y0)   (y0 + y1 is not renormalised). */
+tfo_tf tfo_dpf1(double x0, double x1, double y0, double y1) {
+    tfo_tf z;
+    double q, r0;
+    tfo_div_rem(x0, y0, &q, &r0);
+    double r1 = fma(-q, y1, x1);
+    double c0 = r0 + r1;
+    z.z0 = q;
+    z.z1 = c0 / y0;
+    return z;
+}
+
 /* RPF1 (coupled input): z0 = sqrt(x0); z1 = (x1 (+) fma(x0 - z0^2)) / (2 z0). */
 tfo_tf tfo_rpf1(double x0, double x1) {
     tfo_tf z;
@@ -269,10 +315,45 @@ static tfo_tf op_kinds(int op, double x0, double x1, int xd, double y0, double y
     }
 }
 
+/* Renormalise z0 + z1 with Fast Two-Sum (R10). */
+static tfo_tf renorm(tfo_tf z) {
+    tfo_tf r;
+    tfo_fast_two_sum(z.z0, z.z1, &r.z0, &r.z1);
+    return r;
+}
+
+/* Coupled ("p") operations, R10: op = TFO_PADD .. TFO_PSQRT. */
+enum { TFO_PADD = 6, TFO_PSUB = 7, TFO_PMUL = 8, TFO_PDIV = 9, TFO_PSQRT = 10 };
+
+static tfo_tf op_coupled(int op, double x0, double x1, int xd, double y0, double y1, int yd) {
+    int base = op - 5;
+    if (base == TFO_SQRT) return xd ? tfo_rpf11(x0) : renorm(tfo_rpf1(x0, x1));
+    if (xd && yd) return op_kinds(base, x0, x1, 1, y0, y1, 1);     /* already coupled */
+    if (yd) {
+        switch (base) {
+        case TFO_ADD: return renorm(tfo_atf11(x0, x1, y0));
+        case TFO_SUB: return renorm(tfo_stf11(x0, x1, y0));
+        case TFO_MUL: return renorm(tfo_mtf11(x0, x1, y0));     /* MPF1.1 = MTF1.1 */
+        default:      return renorm(tfo_dtf11(x0, x1, y0));     /* DPF1.1 = DTF1.1 */
+        }
+    }
+    if (xd) x1 = 0.0;
+    switch (base) {
+    case TFO_ADD: return renorm(tfo_atf1(x0, x1, y0, y1));
+    case TFO_SUB: return renorm(tfo_stf1(x0, x1, y0, y1));
+    case TFO_MUL: return renorm(tfo_mpf1(x0, x1, y0, y1));
+    default:      return renorm(tfo_dpf1(x0, x1, y0, y1));
+    }
+}
+
+static tfo_tf op_any(int op, double x0, double x1, int xd, double y0, double y1, int yd) {
+    return op >= TFO_PADD ? op_coupled(op, x0, x1, xd, y0, y1, yd) : op_kinds(op, x0, x1, xd, y0, y1, yd);
+}
+
 /* Scalar entry for tests: kinds xd/yd = 1 means dotted. */
 void tfo_op(int op, double x0, double x1, int xd, double y0, double y1, int yd,
             double *z0, double *z1) {
-    tfo_tf z = op_kinds(op, x0, x1, xd, y0, y1, yd);
+    tfo_tf z = op_any(op, x0, x1, xd, y0, y1, yd);
     *z0 = z.z0;
     *z1 = z.z1;
 }
@@ -321,8 +402,8 @@ void tfo_ew(const int32_t *prog, int nprog, const double *const *in_hi,
         for (int s = 0; s < nprog; ++s) {
             int op = prog[4 * s], a = prog[4 * s + 2], b = prog[4 * s + 3];
             dst = prog[4 * s + 1];
-            if (op == TFO_SQRT) b = a;      /* unary: the second operand is unused */
-            tfo_tf z = op_kinds(op, r0[a], r1[a], dotted[a], r0[b], r1[b], dotted[b]);
+            if (op == TFO_SQRT || op == TFO_PSQRT) b = a;   /* unary: the second operand is unused */
+            tfo_tf z = op_any(op, r0[a], r1[a], dotted[a], r0[b], r1[b], dotted[b]);
             r0[dst] = z.z0;
             r1[dst] = z.z1;
             dotted[dst] = 0;
@@ -343,6 +424,7 @@ void tfo_ew_plain(const int32_t *prog, int nprog, const double *const *in_hi, in
         for (int s = 0; s < nprog; ++s) {
             int op = prog[4 * s], a = prog[4 * s + 2], b = prog[4 * s + 3];
             dst = prog[4 * s + 1];
+            if (op >= TFO_PADD) op -= 5;    /* the plain twin of a coupled op is the basic op */
             if (op == TFO_SQRT) b = a;
             double v;
             switch (op) {

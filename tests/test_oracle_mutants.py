@@ -10,6 +10,7 @@ import pytest
 import oracle as O
 from tests import test_oracle_algorithms as TA
 from tests import test_oracle_applications as TP
+from tests import test_oracle_coupled as TC
 from tests import test_oracle_horner_ew as TH
 from tests import test_oracle_reduce as TR
 from tests import test_oracle_transforms as TT
@@ -78,6 +79,16 @@ MUTANTS = {
     "stf11_adds_instead": (("tfo_stf11", "tfo_two_diff(x0, y0, &d, &e);",
                             "tfo_two_sum(x0, y0, &d, &e);"),
                            [lambda: TA.test_stf11_strict(data())]),
+    "renorm_skipped": (("renorm", "tfo_fast_two_sum(z.z0, z.z1, &r.z0, &r.z1);", "r = z;"),
+                       [lambda: TC.test_coupled_outputs_are_coupled(TC.make_coupled(), O.PADD, "add", "tt")]),
+    "fast_two_sum_swapped": (("tfo_fast_two_sum", "double b1 = s_ - a;", "double b1 = s_ - b;"),
+                             [TC.test_fast_two_sum_exact_when_ordered]),
+    "mpf1_drops_p10": (("tfo_mpf1", "double v = p01 + p10;", "double v = p01;"),
+                       [lambda: TC.test_mpf1_budget(TC.make_coupled())]),
+    "dpf1_r1_sign": (("tfo_dpf1", "fma(-q, y1, x1)", "fma(q, y1, x1)"),
+                     [lambda: TC.test_dpf1_budget(TC.make_coupled())]),
+    "rpf1_drops_x1": (("tfo_rpf1", "double t = x1 + d;", "double t = d;"),
+                      [lambda: TC.test_rpf1_budget(TC.make_coupled())]),
     "gauss_dtf1_drops_d0": (("tfo_dtf1", "double d0 = y0 + y1;", "double d0 = y0 + y0;"),
                             [lambda: TP.test_gauss_logs("gauss_well3", 0.1, (11.0, 11.0, 1.0)),
                              lambda: TA.test_dtf1_budget(data())]),
