@@ -122,11 +122,23 @@ int twofold_host_mapped(const void *ptr);
  * Two-Product) or DTF 1.1.1.  Only inputs can be dotted; every
  * intermediate is a general twofold.
  *
+ * Coupled ("p", Dekker emulation) operations, the paper's p-prefixed
+ * functions (Dekker arithmetic section, Algorithms, Applications): the
+ * algorithm for non-overlapping operands, then the result renormalised with
+ * Fast Two-Sum (Algorithm 1.1, its three operations as printed):
+ *   TF_PADD  ATF 1 (ATF 1.1)      TF_PSUB  STF 1 (STF 1.1)
+ *   TF_PMUL  MPF 1 (MTF 1.1)      TF_PDIV  DPF 1 (DTF 1.1)
+ *   TF_PSQRT RPF 1
+ * (in brackets: b dotted).  With every operand dotted the exact transform,
+ * DTF 1.1.1 or RPF 1.1 is returned unrenormalised (already coupled).  Their
+ * z0 is the renormalised head, not the plain result; plain_ew evaluates
+ * them as the basic operation.
+ *
  * prog    HOST array of nprog instructions, 4 int32 each: {op, dst, a, b}.
  *         Registers 0..nin-1 are the inputs (read only); registers
  *         nin..TF_EW_MAX_REGS-1 are temporaries.  a and b must name an input
  *         or a temporary written by an earlier instruction; b is ignored
- *         for TF_SQRT.  The result is the last instruction's dst.
+ *         for TF_SQRT and TF_PSQRT.  The result is the last instruction's dst.
  * nprog   1..TF_EW_MAX_PROG.
  * in      HOST array of nin tf_in descriptors (device data pointers).
  * nin     1..TF_EW_MAX_INPUTS.
@@ -135,15 +147,17 @@ int twofold_host_mapped(const void *ptr);
  * p       panic parameters (NULL: defaults).
  * Errors: TF_EINVAL for a malformed program or bad pointers.
  */
-enum { TF_ADD = 1, TF_SUB = 2, TF_MUL = 3, TF_DIV = 4, TF_SQRT = 5 };
+enum { TF_ADD = 1, TF_SUB = 2, TF_MUL = 3, TF_DIV = 4, TF_SQRT = 5,
+       TF_PADD = 6, TF_PSUB = 7, TF_PMUL = 8, TF_PDIV = 9, TF_PSQRT = 10 };
 enum { TF_EW_MAX_PROG = 32, TF_EW_MAX_INPUTS = 12, TF_EW_MAX_REGS = 32 };
 
 int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, int32_t nin,
                int64_t n, tf_out out, const tf_params *p, void *stream);
 
 /* Plain binary64 twin of twofold_ew: the same program on the hi arrays
- * only (in: HOST array of nin device pointers), out[i] = the plain result.
- * It equals twofold_ew's z0 bit for bit. */
+ * only (in: HOST array of nin device pointers), out[i] = the plain result
+ * (a coupled op evaluates as its basic op).  It equals twofold_ew's z0 bit
+ * for bit for programs without coupled ops. */
 int plain_ew(const int32_t *prog, int32_t nprog, const double *const *in, int32_t nin,
              int64_t n, double *out, void *stream);
 

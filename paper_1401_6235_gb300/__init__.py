@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libtwofold.so")
 
 TF_OK, TF_EINVAL, TF_ENOSPC, TF_ECUDA, TF_ETIMEOUT, TF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 ADD, SUB, MUL, DIV, SQRT = 1, 2, 3, 4, 5
+PADD, PSUB, PMUL, PDIV, PSQRT = 6, 7, 8, 9, 10      # coupled (Dekker emulation) operations
 PANIC, NONFINITE = 1, 2
 PANIC_REL, PANIC_ULP = 0, 1
 KIND_SUM, KIND_DOT = 1, 2

@@ -188,11 +188,42 @@ __device__ __forceinline__ d2 rtf1(double x0, double x1) {
     return {z0, __dadd_rn(w.z0, w.z1)};
 }
 
+// -------------------------------------------- coupled (Dekker emulation)
+
+// Algorithm 1.1 (Fast Two-Sum), its three operations taken literally: the
+// renormalisation of a twofold (exact when |a| >= |b|).
+__device__ __forceinline__ d2 fast_two_sum(double a, double b) {
+    const double s = __dadd_rn(a, b);
+    const double bv = __dsub_rn(s, a);
+    return {s, __dsub_rn(b, bv)};
+}
+__device__ __forceinline__ d2 renorm(d2 z) { return fast_two_sum(z.z0, z.z1); }
+
+// MPF1 (coupled x, y): z0 = p00;  z1 = e00 + (p01 + p10)  (p11 omitted).
+__device__ __forceinline__ d2 mpf1(double x0, double x1, double y0, double y1) {
+    double p00, e00;
+    two_prod(x0, y0, p00, e00);
+    const double p01 = __dmul_rn(x0, y1);
+    const double p10 = __dmul_rn(x1, y0);
+    return {p00, __dadd_rn(e00, __dadd_rn(p01, p10))};
+}
+
+// DPF1 (coupled x, y): z0 = x0/y0; r0 = fma(-z0, y0, x0); r1 = fma(-z0, y1, x1);
+//       c0 = r0 + r1; z1 = c0/y0  (both divisions by y0 share one reciprocal).
+__device__ __forceinline__ d2 dpf1(double x0, double x1, double y0, double y1) {
+    const uint64_t yb = soft::recip_of(y0);
+    double r0;
+    const double q = soft::div_rn_y(x0, y0, yb, &r0);
+    const double r1 = __fma_rn(-q, y1, x1);
+    return {q, soft::div_rn_y(__dadd_rn(r0, r1), y0, yb)};
+}
+
 // ------------------------------------------------------- operand kinds
 // Operand kinds: (twofold, twofold) general; (twofold, dotted) ".1";
 // (dotted, twofold) general with x1 = +0; (dotted, dotted) exact transform
 // or DTF1.1.1; sqrt of dotted: RPF1.1.
-enum Op : int { OP_ADD = 1, OP_SUB = 2, OP_MUL = 3, OP_DIV = 4, OP_SQRT = 5 };
+enum Op : int { OP_ADD = 1, OP_SUB = 2, OP_MUL = 3, OP_DIV = 4, OP_SQRT = 5,
+               OP_PADD = 6, OP_PSUB = 7, OP_PMUL = 8, OP_PDIV = 9, OP_PSQRT = 10 };
 
 __device__ __forceinline__ d2 apply(int op, double x0, double x1, bool xd, double y0, double y1,
                                     bool yd) {
@@ -223,8 +254,44 @@ __device__ __forceinline__ d2 apply(int op, double x0, double x1, bool xd, doubl
     }
 }
 
+// Coupled ("p") operations, op = OP_PADD .. OP_PSQRT: the coupled variant of
+// the operand kinds, then Fast Two-Sum renormalisation; with every operand
+// dotted the output is already coupled and is returned as is.
+__device__ __forceinline__ d2 apply_coupled(int op, double x0, double x1, bool xd, double y0, double y1,
+                                            bool yd) {
+    const int base = op - 5;
+    if (base == OP_SQRT) return xd ? rpf11(x0) : renorm(rpf1(x0, x1));
+    if (xd && yd) return apply(base, x0, x1, true, y0, y1, true);
+    if (yd) {
+        switch (base) {
+        case OP_ADD: return renorm(atf11(x0, x1, y0));
+        case OP_SUB: return renorm(stf11(x0, x1, y0));
+        case OP_MUL: return renorm(mtf11(x0, x1, y0));         // MPF1.1 = MTF1.1
+        default: return renorm(dtf11(x0, x1, y0));             // DPF1.1 = DTF1.1
+        }
+    }
+    if (xd) x1 = 0.0;
+    switch (base) {
+    case OP_ADD: return renorm(atf1(x0, x1, y0, y1));
+    case OP_SUB: return renorm(stf1(x0, x1, y0, y1));
+    case OP_MUL: return renorm(mpf1(x0, x1, y0, y1));
+    default: return renorm(dpf1(x0, x1, y0, y1));
+    }
+}
+
+// Any operation; P: the program contains coupled operations (kernels without
+// them do not carry their code).
+template <bool P>
+__device__ __forceinline__ d2 apply_any(int op, double x0, double x1, bool xd, double y0, double y1, bool yd) {
+    if (P && op > OP_SQRT) return apply_coupled(op, x0, x1, xd, y0, y1, yd);
+    return apply(op, x0, x1, xd, y0, y1, yd);
+}
+
+__device__ __forceinline__ bool unary(int op) { return op == OP_SQRT || op == OP_PSQRT; }
+
 // Plain binary64 operation (the "dotted" arithmetic the twofold shadows).
 __device__ __forceinline__ double apply_plain(int op, double a, double b) {
+    if (op > OP_SQRT) op -= 5;      // the plain twin of a coupled op is the basic op
     switch (op) {
     case OP_ADD: return __dadd_rn(a, b);
     case OP_SUB: return __dsub_rn(a, b);

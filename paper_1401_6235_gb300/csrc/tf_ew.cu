@@ -24,6 +24,7 @@ struct EwArgs {
     tf::FlagCfg fc;
 };
 
+template <bool P>
 __global__ void __launch_bounds__(kThreads) ew_kernel(const __grid_constant__ EwArgs A) {
     extern __shared__ double regs[];   // [ntemp][2][kThreads]
     const int t = threadIdx.x;
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(kThreads) ew_kernel(const __grid_constant__ Ew
                 x0 = regs[((ra - A.nin) * 2 + 0) * kThreads + t];
                 x1 = regs[((ra - A.nin) * 2 + 1) * kThreads + t];
             }
-            if (op != tf::OP_SQRT) {
+            if (!tf::unary(op)) {
                 if (rb < A.nin) {
                     y0 = A.hi[rb][i];
                     yd = A.lo[rb] == nullptr;
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(kThreads) ew_kernel(const __grid_constant__ Ew
                     yd = false;
                 }
             }
-            tf::d2 z = tf::apply(op, x0, x1, xd, y0, y1, yd);
+            tf::d2 z = tf::apply_any<P>(op, x0, x1, xd, y0, y1, yd);
             const int rd = A.dst[s] - A.nin;
             regs[(rd * 2 + 0) * kThreads + t] = z.z0;
             regs[(rd * 2 + 1) * kThreads + t] = z.z1;
@@ -80,6 +81,7 @@ struct ChainArgs {
     tf::FlagCfg fc;
 };
 
+template <bool P>
 __global__ void __launch_bounds__(kThreads) chain_kernel(const __grid_constant__ ChainArgs A) {
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * kThreads) {
         double x0 = A.hi[A.first][i], x1 = 0.0;
@@ -89,13 +91,13 @@ __global__ void __launch_bounds__(kThreads) chain_kernel(const __grid_constant__
             const int op = A.op[s];
             double y0 = 0.0, y1 = 0.0;
             bool yd = true;
-            if (op != tf::OP_SQRT) {
+            if (!tf::unary(op)) {
                 const int k = A.in[s];
                 y0 = A.hi[k][i];
                 yd = A.lo[k] == nullptr;
                 if (!yd) y1 = A.lo[k][i];
             }
-            const tf::d2 z = tf::apply(op, x0, x1, xd, y0, y1, yd);
+            const tf::d2 z = tf::apply_any<P>(op, x0, x1, xd, y0, y1, yd);
             x0 = z.z0;
             x1 = z.z1;
             xd = false;
@@ -113,9 +115,10 @@ bool as_chain(const int8_t *op, const int8_t *dst, const int8_t *a, const int8_t
     C.first = a[0];
     for (int s = 0; s < nprog; ++s) {
         if (s > 0 && a[s] != dst[s - 1]) return false;
-        if (op[s] != TF_SQRT && b[s] >= nin) return false;
+        const bool un = op[s] == TF_SQRT || op[s] == TF_PSQRT;
+        if (!un && b[s] >= nin) return false;
         C.op[s] = op[s];
-        C.in[s] = op[s] == TF_SQRT ? 0 : b[s];
+        C.in[s] = un ? 0 : b[s];
     }
     C.nsteps = nprog;
     return true;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) plain_ew_kernel(const __grid_constan
             const int op = A.op[s], ra = A.a[s], rb = A.b[s];
             const double x = ra < A.nin ? A.in[ra][i] : regs[(ra - A.nin) * kThreads + t];
             double y = 0.0;
-            if (op != tf::OP_SQRT) y = rb < A.nin ? A.in[rb][i] : regs[(rb - A.nin) * kThreads + t];
+            if (!tf::unary(op)) y = rb < A.nin ? A.in[rb][i] : regs[(rb - A.nin) * kThreads + t];
             regs[(A.dst[s] - A.nin) * kThreads + t] = tf::apply_plain(op, x, y);
         }
         A.out[i] = regs[(A.last - A.nin) * kThreads + t];
@@ -154,10 +157,10 @@ int check_prog(const int32_t *prog, int nprog, int nin, int8_t *op, int8_t *dst,
     for (int s = 0; s < nprog; ++s) {
         const int32_t o = prog[4 * s], d = prog[4 * s + 1], ra = prog[4 * s + 2];
         int32_t rb = prog[4 * s + 3];
-        if (o < TF_ADD || o > TF_SQRT) return -1;
+        if (o < TF_ADD || o > TF_PSQRT) return -1;
         if (d < nin || d >= TF_EW_MAX_REGS) return -1;
         if (ra < 0 || ra >= TF_EW_MAX_REGS || !defined[ra]) return -1;
-        if (o == TF_SQRT) rb = ra;
+        if (o == TF_SQRT || o == TF_PSQRT) rb = ra;
         if (rb < 0 || rb >= TF_EW_MAX_REGS || !defined[rb]) return -1;
         defined[d] = true;
         if (d > maxreg) maxreg = d;
@@ -195,21 +198,26 @@ extern "C" int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, i
     A.n = n; A.nprog = nprog; A.nin = nin;
     A.out_hi = out.hi; A.out_lo = out.lo; A.flags = out.flags;
     A.fc = tfh::flag_cfg(p);
+    bool coupled = false;
+    for (int q = 0; q < nprog; ++q) coupled |= A.op[q] > TF_SQRT;
+    cudaStream_t st = tfh::as_stream(stream);
     ChainArgs C{};
     if (as_chain(A.op, A.dst, A.a, A.b, nprog, nin, C)) {
         C.n = n;
         for (int k = 0; k < nin; ++k) { C.hi[k] = A.hi[k]; C.lo[k] = A.lo[k]; }
         C.out_hi = A.out_hi; C.out_lo = A.out_lo; C.flags = A.flags; C.fc = A.fc;
-        const int grid = grid_for(n, 0, (const void *)chain_kernel);
-        chain_kernel<<<grid, kThreads, 0, tfh::as_stream(stream)>>>(C);
+        if (coupled) chain_kernel<true><<<grid_for(n, 0, (const void *)chain_kernel<true>), kThreads, 0, st>>>(C);
+        else chain_kernel<false><<<grid_for(n, 0, (const void *)chain_kernel<false>), kThreads, 0, st>>>(C);
         return tfh::launch_status();
     }
     const size_t smem = (size_t)A.ntemp * 2 * kThreads * sizeof(double);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(ew_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const void *kern = coupled ? (const void *)ew_kernel<true> : (const void *)ew_kernel<false>;
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                                cudaSuccess)
         return TF_ECUDA;
-    const int grid = grid_for(n, smem, (const void *)ew_kernel);
-    ew_kernel<<<grid, kThreads, smem, tfh::as_stream(stream)>>>(A);
+    const int grid = grid_for(n, smem, kern);
+    if (coupled) ew_kernel<true><<<grid, kThreads, smem, st>>>(A);
+    else ew_kernel<false><<<grid, kThreads, smem, st>>>(A);
     return tfh::launch_status();
 }
 

@@ -60,7 +60,8 @@ def _call_ew(L, rows, nin=2, n=10, out_hi=FAKE, in_lo=None):
 
 
 @pytest.mark.parametrize("rows", [
-    [(9, 2, 0, 1)],                 # unknown op
+    [(11, 2, 0, 1)],                # unknown op
+    [(0, 2, 0, 1)],                 # unknown op
     [(1, 1, 0, 1)],                 # writes an input register
     [(1, 2, 0, 3)],                 # reads an undefined register
     [(1, 40, 0, 1)],                # register out of range

@@ -118,6 +118,72 @@ def test_host_buffer_form_equals_device_buffers():
         T.twofold_ew(T.CHAIN_SQRT_MAD_DIV, [(torch.from_numpy(h), None) for h, _ in ins])
 
 
+def coupled_operands(n=100003, seed=5):
+    """Non-overlapping ("coupled") operands: |tail| <= ulp(head)/2."""
+    rng = np.random.default_rng(seed)
+    x0 = rand_doubles(rng, n, -80, 80)
+    y0 = rand_doubles(rng, n, -80, 80)
+    ux = np.ldexp(1.0, np.frexp(np.abs(x0))[1] - 53)
+    uy = np.ldexp(1.0, np.frexp(np.abs(y0))[1] - 53)
+    return x0, ux / 2 * rng.uniform(-1, 1, n), y0, uy / 2 * rng.uniform(-1, 1, n)
+
+
+@pytest.mark.parametrize("op", [O.PADD, O.PSUB, O.PMUL, O.PDIV, O.PSQRT])
+@pytest.mark.parametrize("xd,yd", list(itertools.product([False, True], repeat=2)))
+@pytest.mark.parametrize("data", ["edge", "random", "coupled"])
+def test_coupled_op_kinds(op, xd, yd, data):
+    """Coupled (Dekker emulation) operations, every operand kind, special
+    values, general twofolds and non-overlapping ones: bit-exact."""
+    x0, x1, y0, y1 = {"edge": edge_operands, "random": random_operands, "coupled": coupled_operands}[data]()
+    prog = [(op, 2, 0, 1 if op != O.PSQRT else 0)]
+    ins = [(x0, None if xd else x1), (y0, None if yd else y1)]
+    r0, r1, rf = O.ew(prog, ins)
+    g = [(dev(h), None if lo is None else dev(lo)) for h, lo in ins]
+    z0, z1, fl = T.twofold_ew(prog, g)
+    assert_bits(z0, r0, "z0")
+    assert_bits(z1, r1, "z1")
+    assert_flags(fl, rf, "flags")
+
+
+def test_coupled_chain_and_mixed_programs():
+    """A chain of coupled ops (chain kernel) and random programs mixing
+    twofold and coupled ops (interpreter): bit-exact; the plain twin of a
+    coupled op is its basic op."""
+    n = 50021
+    d = synth.ew_chain(n, seed=13)
+    ins = [(d[k + "0"], d[k + "1"]) for k in "abcd"]
+    pchain = [(O.PMUL, 4, 0, 1), (O.PADD, 5, 4, 2), (O.PDIV, 6, 5, 3), (O.PSQRT, 7, 6, 6)]
+    r0, r1, rf = O.ew(pchain, ins)
+    g = [(dev(h), dev(lo)) for h, lo in ins]
+    z0, z1, fl = T.twofold_ew(pchain, g)
+    assert_bits(z0, r0, "p-chain z0")
+    assert_bits(z1, r1, "p-chain z1")
+    assert_flags(fl, rf, "p-chain flags")
+    assert_bits(T.plain_ew(pchain, [h for h, _ in g]), O.ew_plain(T.CHAIN_SQRT_MAD_DIV, [h for h, _ in ins]),
+                "plain twin")
+    rng = np.random.default_rng(17)
+    m = 20011
+    for trial in range(8):
+        nin = int(rng.integers(1, 5))
+        ins_np = []
+        for k in range(nin):
+            h = np.abs(rand_doubles(rng, m, -6, 6))
+            lo = None if rng.random() < 0.3 else rand_tails(rng, h, 40, 60)
+            ins_np.append((h, lo))
+        prog, defined = [], list(range(nin))
+        for s_ in range(int(rng.integers(1, 9))):
+            op = int(rng.integers(1, 11))
+            a, b = int(rng.choice(defined)), int(rng.choice(defined))
+            prog.append((op, nin + s_, a, a if op in (O.SQRT, O.PSQRT) else b))
+            defined.append(nin + s_)
+        r0, r1, rf = O.ew(prog, ins_np)
+        gg = [(dev(h), None if lo is None else dev(lo)) for h, lo in ins_np]
+        z0, z1, fl = T.twofold_ew(prog, gg)
+        assert_bits(z0, r0, f"trial {trial} z0")
+        assert_bits(z1, r1, f"trial {trial} z1")
+        assert_flags(fl, rf, f"trial {trial} flags")
+
+
 @pytest.mark.parametrize("mode", [T.PANIC_REL, T.PANIC_ULP])
 def test_chain_flag_modes(mode):
     n = 50001
