@@ -47,10 +47,10 @@ class _TF(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FP contraction, no fast-math)."""
-    src = os.path.join(_HERE, "twofold_oracle.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+    srcs = [os.path.join(_HERE, f) for f in ("twofold_oracle.c", "twofold_oracle_f32.c")]
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(s) for s in srcs):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, src, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, *srcs, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -97,6 +97,17 @@ def load(path: str) -> ctypes.CDLL:
     L.tfo_reduce_plain.restype = d
     L.tfo_horner.argtypes = [p, i, p, i64, i64, p, p, p, i, d, d]
     L.tfo_horner_plain.argtypes = [p, i, p, i64, i64, p]
+    f = ctypes.c_float
+    pf = ctypes.POINTER(ctypes.c_float)
+    for name in ("tfof_two_sum", "tfof_two_diff", "tfof_two_prod", "tfof_div_rem", "tfof_fast_two_sum"):
+        getattr(L, name).argtypes = [f, f, pf, pf]
+    L.tfof_sqrt_rem.argtypes = [f, pf, pf]
+    L.tfof_op.argtypes = [i, f, f, i, f, f, i, pf, pf]
+    L.tfof_flag.argtypes = [f, f, i, f, f]
+    L.tfof_flag.restype = ctypes.c_ubyte
+    L.tfof_ew.argtypes = [p, i, p, p, i, i64, i64, p, p, p, i, f, f]
+    L.tfof_ew_plain.argtypes = [p, i, p, i, i64, i64, p]
+    L.tfof_reduce_sum.argtypes = [p, p, i64, i64, pf, pf]
     return L
 
 
@@ -349,3 +360,81 @@ def horner_batched(coefs, coef_offs, ks, x, x_offs, mode=REL, tau=DEFAULT_TAU, m
         s, e = int(x_offs[j]), int(x_offs[j + 1])
         z0[s:e], z1[s:e], fl[s:e] = horner(a, x[s:e], mode, tau, m, threads)
     return z0, z1, fl
+
+
+# ------------------------------------------------------------ binary32 basis
+
+STICKY = 4           # flag mode bit: OR the flags of every intermediate result (R12)
+DEFAULT_TAU32 = 2.0 ** -18
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _pair32(fn, *args):
+    a, b = ctypes.c_float(), ctypes.c_float()
+    fn(*args, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def two_sum32(a, b): return _pair32(lib().tfof_two_sum, a, b)
+def two_diff32(a, b): return _pair32(lib().tfof_two_diff, a, b)
+def two_prod32(a, b): return _pair32(lib().tfof_two_prod, a, b)
+def div_rem32(a, b): return _pair32(lib().tfof_div_rem, a, b)
+def sqrt_rem32(a): return _pair32(lib().tfof_sqrt_rem, a)
+def fast_two_sum32(a, b): return _pair32(lib().tfof_fast_two_sum, a, b)
+
+
+def op32(code, x, y=None):
+    """One binary32 twofold op (operands as in op()); returns (z0, z1) as floats
+    holding binary32 values."""
+    def split(v):
+        if v is None:
+            return 0.0, 0.0, 1
+        if isinstance(v, tuple):
+            return float(v[0]), float(v[1]), 0
+        return float(v), 0.0, 1
+    x0, x1, xd = split(x)
+    y0, y1, yd = split(y)
+    return _pair32(lib().tfof_op, code, x0, x1, xd, y0, y1, yd)
+
+
+def flag32(z0, z1, mode=REL, tau=DEFAULT_TAU32, m=1.0):
+    return int(lib().tfof_flag(z0, z1, mode, tau, m))
+
+
+def ew32(prog, inputs, mode=REL, tau=DEFAULT_TAU32, m=1.0, threads=None):
+    """binary32 twofold program (inputs: (hi, lo-or-None) float32 arrays)."""
+    prog_a = np.ascontiguousarray(np.asarray(prog, np.int32).reshape(-1, 4))
+    his = [_f32(h) for h, _ in inputs]
+    los = [None if lo is None else _f32(lo) for _, lo in inputs]
+    n = his[0].size if his else 0
+    hp = (ctypes.c_void_p * len(his))(*[_ptr(h) for h in his])
+    lp = (ctypes.c_void_p * len(los))(*[_ptr(lo) for lo in los])
+    z0 = np.empty(n, np.float32)
+    z1 = np.empty(n, np.float32)
+    fl = np.empty(n, np.uint8)
+    L = lib()
+    _par(n, lambda s, e: L.tfof_ew(_ptr(prog_a), prog_a.shape[0], hp, lp, len(his), s, e, _ptr(z0), _ptr(z1),
+                                   _ptr(fl), mode, tau, m), threads=threads)
+    return z0, z1, fl
+
+
+def ew32_plain(prog, his, threads=None):
+    prog_a = np.ascontiguousarray(np.asarray(prog, np.int32).reshape(-1, 4))
+    his = [_f32(h) for h in his]
+    n = his[0].size if his else 0
+    hp = (ctypes.c_void_p * len(his))(*[_ptr(h) for h in his])
+    out = np.empty(n, np.float32)
+    L = lib()
+    _par(n, lambda s, e: L.tfof_ew_plain(_ptr(prog_a), prog_a.shape[0], hp, len(his), s, e, _ptr(out)),
+         threads=threads)
+    return out
+
+
+def reduce_sum32(x, xl=None, L=256):
+    """binary32 twofold sum in the blocked pairwise order (R8)."""
+    x = _f32(x)
+    xl = None if xl is None else _f32(xl)
+    return _pair32(lib().tfof_reduce_sum, _ptr(x), _ptr(xl), x.size, L)

@@ -48,6 +48,8 @@
  *      operand dotted the output of the exact transform / DTF 1.1.1 / RPF 1.1
  *      is already coupled and is returned as is (Applications; the pdiv of
  *      two dotted numbers in Fragment 4 returns tdiv unchanged).
+ *  R12 Sticky flag (mode bit 4): a program's flag ORs the flags of every
+ *      instruction's result (twofold_oracle_f32.c holds the binary32 basis).
  */
 #include <math.h>
 #include <stdint.h>
@@ -370,11 +372,12 @@ static double ulp_of(double v) {
     return ldexp(1.0, e - 1075);
 }
 
-/* mode 0 = REL (|z1| > tau*|z0|), 1 = ULP (|z1| > m*ulp(z0)). */
+/* mode & 3: 0 = REL (|z1| > tau*|z0|), 1 = ULP (|z1| > m*ulp(z0)); mode & 4:
+ * sticky (R12, applied by the program evaluator). */
 unsigned char tfo_flag(double z0, double z1, int mode, double tau, double m) {
     unsigned char f = 0;
     if (!isfinite(z0) || !isfinite(z1)) f |= TFO_NONFINITE;
-    double lim = (mode == 0) ? tau * fabs(z0) : m * ulp_of(z0);
+    double lim = ((mode & 3) == 0) ? tau * fabs(z0) : m * ulp_of(z0);
     if (fabs(z1) > lim) f |= TFO_PANIC;
     return f;
 }
@@ -399,6 +402,7 @@ void tfo_ew(const int32_t *prog, int nprog, const double *const *in_hi,
             dotted[k] = in_lo[k] == NULL;
         }
         int dst = 0;
+        unsigned char sticky = 0;
         for (int s = 0; s < nprog; ++s) {
             int op = prog[4 * s], a = prog[4 * s + 2], b = prog[4 * s + 3];
             dst = prog[4 * s + 1];
@@ -407,10 +411,11 @@ void tfo_ew(const int32_t *prog, int nprog, const double *const *in_hi,
             r0[dst] = z.z0;
             r1[dst] = z.z1;
             dotted[dst] = 0;
+            if (mode & 4) sticky |= tfo_flag(z.z0, z.z1, mode, tau, m);   /* R12 */
         }
         out_hi[i] = r0[dst];
         out_lo[i] = r1[dst];
-        if (flags) flags[i] = tfo_flag(r0[dst], r1[dst], mode, tau, m);
+        if (flags) flags[i] = (unsigned char)(tfo_flag(r0[dst], r1[dst], mode, tau, m) | sticky);
     }
 }
 

@@ -88,3 +88,43 @@ def fma(a: float, b: float, c: float) -> float:
             return -0.0
         return 0.0
     return rn(q)
+
+
+# ------------------------------------------------------------------ binary32
+
+U32 = Fraction(1, 2 ** 24)        # unit roundoff of binary32
+
+
+def rn32(q: Fraction) -> float:
+    """Round a rational to the nearest binary32 value (ties to even), as a
+    Python float holding that value; overflow gives +-inf."""
+    if q == 0:
+        return 0.0
+    s = -1.0 if q < 0 else 1.0
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    q_exp = max(e, -126) - 23                       # exponent of the ulp
+    m = round(a / Fraction(2) ** q_exp)             # round half to even
+    v = float(Fraction(m) * Fraction(2) ** q_exp)
+    if v > 3.4028234663852886e38:
+        return s * math.inf
+    return s * v
+
+
+def f32(x: float) -> float:
+    return float(np.float32(x))
+
+
+def ulp32(x: float) -> float:
+    if x == 0 or not math.isfinite(x):
+        return 2.0 ** -149 if x == 0 else math.nan
+    m, e = math.frexp(abs(x))
+    return 2.0 ** (max(e - 1, -126) - 23)
+
+
+def split32(v: float):
+    """A double as a binary32 twofold: (float(v), float(v - float(v)))."""
+    h = f32(v)
+    return h, f32(v - h)

@@ -11,11 +11,13 @@ import oracle as O
 from tests import test_oracle_algorithms as TA
 from tests import test_oracle_applications as TP
 from tests import test_oracle_coupled as TC
+from tests import test_oracle_f32 as TF
 from tests import test_oracle_horner_ew as TH
 from tests import test_oracle_reduce as TR
 from tests import test_oracle_transforms as TT
 
 SRC = os.path.join(os.path.dirname(O.__file__), "twofold_oracle.c")
+SRC32 = os.path.join(os.path.dirname(O.__file__), "twofold_oracle_f32.c")
 
 
 def _in_function(src, fname, old, new):
@@ -89,6 +91,14 @@ MUTANTS = {
                      [lambda: TC.test_dpf1_budget(TC.make_coupled())]),
     "rpf1_drops_x1": (("tfo_rpf1", "double t = x1 + d;", "double t = d;"),
                       [lambda: TC.test_rpf1_budget(TC.make_coupled())]),
+    "f32_two_diff_printed_signs": (("tfof_two_diff", "float bs = b1 - b;", "float bs = b - b1;"),
+                                   [lambda: TF.test_exact_transforms32(
+                                       (TF.rand32(__import__("numpy").random.default_rng(1), 3000),
+                                        TF.rand32(__import__("numpy").random.default_rng(2), 3000)))]),
+    "f32_atf1_subtracts_tail": (("tfof_atf1", "float u = x1 + y1;", "float u = x1 - y1;"),
+                                [lambda: TF.test_atf1_stf1_budget32(
+                                    (TF.rand32(__import__("numpy").random.default_rng(1), 3000),
+                                     TF.rand32(__import__("numpy").random.default_rng(2), 3000)))]),
     "gauss_dtf1_drops_d0": (("tfo_dtf1", "double d0 = y0 + y1;", "double d0 = y0 + y0;"),
                             [lambda: TP.test_gauss_logs("gauss_well3", 0.1, (11.0, 11.0, 1.0)),
                              lambda: TA.test_dtf1_budget(data())]),
@@ -98,11 +108,13 @@ MUTANTS = {
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_mutant_is_caught(name, tmp_path):
     (fname, old, new), checks = MUTANTS[name]
-    src = _in_function(open(SRC).read(), fname, old, new)
-    c = tmp_path / "mutant.c"
-    c.write_text(src)
+    srcs = [SRC, SRC32]
+    k = 1 if fname.startswith("tfof_") else 0          # the binary32 basis lives in its own file
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(_in_function(open(srcs[k]).read(), fname, old, new))
+    srcs[k] = str(mutated)
     so = tmp_path / "libmutant.so"
-    subprocess.check_call(["gcc", *O.CFLAGS, str(c), "-o", str(so), "-lm"])
+    subprocess.check_call(["gcc", *O.CFLAGS, *srcs, "-o", str(so), "-lm"])
     saved = O.lib()
     O._lib = O.load(str(so))
     failed = 0
