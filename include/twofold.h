@@ -71,12 +71,15 @@ typedef struct {
  *   TF_PANIC_ULP: PANIC when |z1| > panic_ulps * ulp(z0),
  *                 ulp(v) = 2^(max(e,-1022)-52) for v = 1.f * 2^e, ulp(0) = 2^-1074
  * Both products are single round-to-nearest multiplications.  NaN compares
- * false, so a NaN z1 never raises PANIC; NONFINITE covers it. */
-enum { TF_PANIC_REL = 0, TF_PANIC_ULP = 1 };
+ * false, so a NaN z1 never raises PANIC; NONFINITE covers it.
+ * panic_mode | TF_PANIC_STICKY (elementwise programs): the flag of a result
+ * ORs the flags of every instruction's result of its program, so a loss of
+ * accuracy anywhere in a chain stays visible at its end. */
+enum { TF_PANIC_REL = 0, TF_PANIC_ULP = 1, TF_PANIC_STICKY = 4 };
 enum { TF_FLAG_PANIC = 1, TF_FLAG_NONFINITE = 2 };
 
 typedef struct {
-    int32_t panic_mode;   /* TF_PANIC_REL or TF_PANIC_ULP                      */
+    int32_t panic_mode;   /* TF_PANIC_REL or TF_PANIC_ULP, | TF_PANIC_STICKY   */
     int32_t leaf;         /* leaf length L of sum/dot (>= 1); default 256      */
     double  panic_tau;    /* REL threshold >= 0, default 0x1p-40               */
     double  panic_ulps;   /* ULP threshold m >= 0, default 4096                */
@@ -160,6 +163,31 @@ int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, int32_t nin,
  * for bit for programs without coupled ops. */
 int plain_ew(const int32_t *prog, int32_t nprog, const double *const *in, int32_t nin,
              int64_t n, double *out, void *stream);
+
+/* ------------------------------------------- binary32 elementwise programs
+ *
+ * The same programs, operations, operand kinds and flags over binary32
+ * twofolds (the paper's algorithms are generic over the number type; its
+ * logs print float rows).  Every operation is a round-to-nearest binary32
+ * operation with subnormals kept.  Flags: tau and ulps of `p` are rounded to
+ * binary32; with p == NULL, tau = 2^-18 (the share of binary32's 24-bit
+ * significand that 2^-40 is of binary64's 53) and ulps = 4096.  Pointers
+ * are 4-byte aligned device (or mapped host) pointers. */
+typedef struct {
+    const float *hi;
+    const float *lo;
+} tf_in_f32;
+
+typedef struct {
+    float *hi;
+    float *lo;
+    uint8_t *flags;
+} tf_out_f32;
+
+int twofold_ew_f32(const int32_t *prog, int32_t nprog, const tf_in_f32 *in, int32_t nin,
+                   int64_t n, tf_out_f32 out, const tf_params *p, void *stream);
+int plain_ew_f32(const int32_t *prog, int32_t nprog, const float *const *in, int32_t nin,
+                 int64_t n, float *out, void *stream);
 
 /* ------------------------------------------------------ sum and dot
  *

@@ -24,7 +24,7 @@ TF_OK, TF_EINVAL, TF_ENOSPC, TF_ECUDA, TF_ETIMEOUT, TF_EUNSUPPORTED = 0, -1, -2,
 ADD, SUB, MUL, DIV, SQRT = 1, 2, 3, 4, 5
 PADD, PSUB, PMUL, PDIV, PSQRT = 6, 7, 8, 9, 10      # coupled (Dekker emulation) operations
 PANIC, NONFINITE = 1, 2
-PANIC_REL, PANIC_ULP = 0, 1
+PANIC_REL, PANIC_ULP, PANIC_STICKY = 0, 1, 4
 KIND_SUM, KIND_DOT = 1, 2
 MAX_PROG, MAX_INPUTS, MAX_REGS = 32, 12, 32
 
@@ -43,6 +43,14 @@ class tf_in(ctypes.Structure):
 
 
 class tf_out(ctypes.Structure):
+    _fields_ = [("hi", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("flags", ctypes.c_void_p)]
+
+
+class tf_in_f32(ctypes.Structure):
+    _fields_ = [("hi", ctypes.c_void_p), ("lo", ctypes.c_void_p)]
+
+
+class tf_out_f32(ctypes.Structure):
     _fields_ = [("hi", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("flags", ctypes.c_void_p)]
 
 
@@ -100,6 +108,8 @@ SIGNATURES = {
     "twofold_host_mapped": ([_P], ctypes.c_int),
     "twofold_ew": ([_P, _I32, _P, _I32, _I64, _OUT, _PP, _P], ctypes.c_int),
     "plain_ew": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
+    "twofold_ew_f32": ([_P, _I32, _P, _I32, _I64, tf_out_f32, _PP, _P], ctypes.c_int),
+    "plain_ew_f32": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
     "twofold_workspace_bytes": ([_I32, _I64, _I32, _PP], _SZ),
     "twofold_sum": ([_IN, _I64, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
     "twofold_dot": ([_IN, _IN, _I64, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
@@ -254,6 +264,46 @@ def plain_ew(prog, his, out=None, stream=None):
                else torch.empty(n, dtype=torch.float64, device=his[0].device))
     _check(lib().plain_ew(pa.ctypes.data, pa.shape[0], ptrs, len(his), n, _dev(out, "out", True),
                           _stream(stream)), "plain_ew")
+    return out
+
+
+def _outputs_f32(n, device, out):
+    torch = _torch()
+    if out is not None:
+        return out
+    if device.type == "cpu":
+        return (torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory(),
+                torch.empty(n, dtype=torch.uint8).pin_memory())
+    return (torch.empty(n, dtype=torch.float32, device=device), torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(n, dtype=torch.uint8, device=device))
+
+
+def twofold_ew_f32(prog, inputs, out=None, p: tf_params | None = None, stream=None):
+    """twofold_ew over binary32 twofolds: inputs are (hi, lo) float32 tensors
+    (lo None for dotted input); returns (z0, z1, flags)."""
+    pa = _prog_array(prog)
+    n = inputs[0][0].numel()
+    for h, lo in inputs:
+        if h.numel() != n or (lo is not None and lo.numel() != n):
+            raise ValueError("inputs must all have the same length")
+    ins = (tf_in_f32 * len(inputs))(*[tf_in_f32(_dev(h, "hi", True), _dev(lo, "lo", True)) for h, lo in inputs])
+    hi, lo_, fl = _outputs_f32(n, inputs[0][0].device, out)
+    o = tf_out_f32(_dev(hi, "out hi", True), _dev(lo_, "out lo", True), _dev(fl, "flags", True))
+    _check(lib().twofold_ew_f32(pa.ctypes.data, pa.shape[0], ins, len(inputs), n, o, _pp(p), _stream(stream)),
+           "twofold_ew_f32")
+    return hi, lo_, fl
+
+
+def plain_ew_f32(prog, his, out=None, stream=None):
+    torch = _torch()
+    pa = _prog_array(prog)
+    n = his[0].numel()
+    ptrs = (ctypes.c_void_p * len(his))(*[_dev(h, "input", True) for h in his])
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float32).pin_memory() if his[0].device.type == "cpu"
+               else torch.empty(n, dtype=torch.float32, device=his[0].device))
+    _check(lib().plain_ew_f32(pa.ctypes.data, pa.shape[0], ptrs, len(his), n, _dev(out, "out", True),
+                              _stream(stream)), "plain_ew_f32")
     return out
 
 

@@ -328,7 +328,7 @@ __device__ __forceinline__ uint8_t flag_of(double z0, double z1, const FlagCfg &
     // tau >= 0, so |RN(tau z0)| = RN(tau |z0|): the magnitude is taken on the
     // bits; a power-of-two tau (the default 2^-40) scales in integer form
     uint64_t l;
-    if (f.mode == 0) {
+    if ((f.mode & 3) == 0) {
         if (f.k <= 0) l = soft::scale_abs_pow2(bits_of(z0), f.k);
         else l = bits_of(__dmul_rn(f.tau, z0)) & 0x7FFFFFFFFFFFFFFFull;
     } else {

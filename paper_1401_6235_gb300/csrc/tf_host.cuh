@@ -12,6 +12,7 @@
 namespace tfh {
 
 constexpr double kDefaultTau = 0x1p-40;
+constexpr float kDefaultTau32 = 0x1p-18f;     // binary32: the same share of the significand as 2^-40 of 53 bits
 constexpr double kDefaultUlps = 4096.0;
 constexpr int kDefaultLeaf = 256;
 
@@ -29,7 +30,8 @@ inline tf::FlagCfg flag_cfg(const tf_params *p) {
 
 inline bool params_ok(const tf_params *p) {
     if (!p) return true;
-    if (p->panic_mode != TF_PANIC_REL && p->panic_mode != TF_PANIC_ULP) return false;
+    if ((p->panic_mode & ~TF_PANIC_STICKY) != TF_PANIC_REL && (p->panic_mode & ~TF_PANIC_STICKY) != TF_PANIC_ULP)
+        return false;
     if (p->leaf < 1) return false;
     if (!(p->panic_tau >= 0.0) || !(p->panic_ulps >= 0.0)) return false;   // also rejects NaN
     return true;
@@ -40,6 +42,12 @@ inline int leaf_of(const tf_params *p) { return p ? p->leaf : kDefaultLeaf; }
 inline bool aligned8(const void *ptr) { return ((uintptr_t)ptr & 7u) == 0; }
 inline bool dptr_ok(const void *ptr) { return ptr != nullptr && aligned8(ptr); }
 inline bool optr_ok(const void *ptr) { return ptr == nullptr || aligned8(ptr); }
+
+// Element pointers of either basis: non-null (or nullable) and aligned to the element.
+template <typename T>
+inline bool fptr_ok(const T *ptr) { return ptr != nullptr && ((uintptr_t)ptr % sizeof(T)) == 0; }
+template <typename T>
+inline bool foptr_ok(const T *ptr) { return ptr == nullptr || ((uintptr_t)ptr % sizeof(T)) == 0; }
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 

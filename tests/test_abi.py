@@ -24,7 +24,7 @@ def L():
 def declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b([a-z_]+)\s*\(", src)) - {"sizeof"})
+    return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", src)) - {"sizeof"})
 
 
 def test_every_declared_symbol_is_exported(L):
