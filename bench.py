@@ -39,6 +39,8 @@ FP64_OPS_PER_CLK_SM = 2.0
 # Algorithmic unit costs (bytes and basic FP64 operations per result).
 EW_BYTES = 8 * 8 + 2 * 8 + 1            # 4 twofold inputs, twofold output, flag byte
 EW_PLAIN_BYTES = 4 * 8 + 8
+EW32_BYTES = 8 * 4 + 2 * 4 + 1          # the binary32 chain: 4 twofold inputs, twofold output, flag
+EW32_PLAIN_BYTES = 4 * 4 + 4
 # basic ops of the chain: MTF1 8, ATF1 8, DTF1 6 (2 div), RTF1 20 (2 sqrt, 1 div), flag 1
 EW_OPS = 8 + 8 + 6 + 20 + 1
 DOT_BYTES = 16                           # dotted x_i, y_i
@@ -51,7 +53,6 @@ HORNER_OPS_PER_STEP = 4 + 7              # MTF1.1 + ATF1.1
 # profiles/), scaled by the units a launch processes; None where the kernel
 # changed after its counters were taken.
 TRAFFIC_PER_UNIT = {
-    "ew_chain": (20.63e9 / (1 << 28), "profiles/chain_kernel_ew_chain_n2e28.md"),
     "horner": (1.571e9 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
     "cond_dots": ((268.58e6 + 3.62e6) / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
     "dot": (1.111e6 / 65536, "profiles/reduce_lat_dot_n65536.md"),
@@ -580,8 +581,54 @@ def workload_serve(args, rank, world, dist_on):
     }
 
 
+def workload_ew_f32(args, rank, world, dist_on):
+    """The chain sqrt((a*b + c)/d) over binary32 twofolds (the paper's float
+    basis): heads float(v), tails float(v - head) of the binary64 chain
+    inputs, 41 B per element (plain twin 20 B).  On this GPU the binary32
+    arithmetic runs on the wide FP32 pipe, so the kernel is bound by HBM."""
+    import torch
+    import paper_1401_6235_gb300 as T
+    import synth
+    n = args.n or (1 << 28)
+    prog = T.CHAIN_SQRT_MAD_DIV
+    g = {k: (torch.empty(n, dtype=torch.float32, device="cuda"), torch.empty(n, dtype=torch.float32, device="cuda"))
+         for k in "abcd"}
+    chunk = 1 << 24
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        d = synth.ew_chain(e - s, seed=rank * 1000 + s // chunk)
+        for k in "abcd":
+            h = d[k + "0"].astype(np.float32)
+            g[k][0][s:e].copy_(torch.from_numpy(h))
+            g[k][1][s:e].copy_(torch.from_numpy((d[k + "0"] - h.astype(np.float64)).astype(np.float32)))
+    ins = [g[k] for k in "abcd"]
+    out = (torch.empty(n, dtype=torch.float32, device="cuda"), torch.empty(n, dtype=torch.float32, device="cuda"),
+           torch.empty(n, dtype=torch.uint8, device="cuda"))
+    pout = torch.empty(n, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    with ClockSampler(args.smi_index) as cs:
+        ms = time_steps(lambda: T.twofold_ew_f32(prog, ins, out=out), args.steps, args.warmup, dist_on)
+    plain_ms = time_steps(lambda: T.plain_ew_f32(prog, [h for h, _ in ins], out=pout), args.steps, args.warmup,
+                          dist_on)
+    per = ms / args.steps
+    nbytes = EW32_BYTES * n
+    return {
+        "metric": "twofold GB/s, binary32 basis (elementwise chain sqrt((a*b+c)/d), 41 B/elt)",
+        "value": nbytes * world / (per * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": per,
+        "plain_ms_per_step": plain_ms / args.steps, "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "plain_gbs": EW32_PLAIN_BYTES * n * world / (plain_ms / args.steps * 1e-3) / 1e9,
+        "config": {"workload": "ew_chain binary32 sqrt((a*b+c)/d)", "n": n, "bytes_per_elt": EW32_BYTES,
+                   "inputs": "the binary64 chain inputs as binary32 twofolds (head float(v), tail float(v-head))",
+                   "l2": "inputs (8 GiB) larger than L2; no flush needed", "parallelism": f"replicas x{world}"},
+        "gpu_launches": args.steps, "clocks": cs.summary(),
+        "_kernel_ms": per, "_ops": 0, "_bytes": nbytes, "_units": n, "_sample": None,
+        "_bound": "hbm", "_dtype": "f32",
+    }
+
+
 WORKLOADS = {"ew_chain": workload_ew, "dot": workload_dot, "cond_dots": workload_cond_dots,
-             "horner": workload_horner, "batch_mix": workload_batch_mix, "serve": workload_serve}
+             "horner": workload_horner, "batch_mix": workload_batch_mix, "serve": workload_serve,
+             "ew_chain_f32": workload_ew_f32}
 
 
 # -------------------------------------------------------------- reference
@@ -663,9 +710,19 @@ def main():
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak_fp64 = FP64_OPS_PER_CLK_SM * sms * clk * 1e6 / 1e12
         achieved = ops / (kms * 1e-3) / 1e12
+        bound = res.pop("_bound", "alu")
         if ops == 0:                                   # a serving line: no single kernel to place
             achieved = None
-        res["roofline"] = None if achieved is None else {
+        if bound == "hbm":
+            gbs = nbytes / (kms * 1e-3) / 1e9
+            res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                               "traffic": traffic, "traffic_source": tr[1] if traffic else None,
+                               "what": f"algorithmic bytes per launch / launch time vs the {src} copy bandwidth"}
+            achieved = None
+        elif achieved is None:
+            res["roofline"] = None
+        if achieved is not None:
+            res["roofline"] = {
             "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
             "frac": achieved / peak_fp64, "traffic": traffic, "traffic_source": tr[1] if traffic else None,
             "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
@@ -677,7 +734,7 @@ def main():
         line = {"metric": res.pop("metric"), "value": res.pop("value"), "unit": res.pop("unit"),
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": res.pop("ms_per_step"), "higher_is_better": res.pop("higher_is_better", True),
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+                "scaling": "weak", "vs_baseline": None, "dtype": res.pop("_dtype", "f64"), "data": "synthetic"}
         line.update(res)
         print(json.dumps(line), flush=True)
     if dist_on:

@@ -157,6 +157,18 @@ enum { TF_EW_MAX_PROG = 32, TF_EW_MAX_INPUTS = 12, TF_EW_MAX_REGS = 32 };
 int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, int32_t nin,
                int64_t n, tf_out out, const tf_params *p, void *stream);
 
+/* Runtime specialisation of elementwise programs: for n >= 2^20 (automatic
+ * mode) twofold_ew and twofold_ew_f32 run a straight-line kernel of the
+ * program, compiled once per distinct program (and operand kinds and flag
+ * mode) at its first such call by the runtime compiler for this GPU from the
+ * library's own device code, and cached for the process; its results are the
+ * generic kernels' bits.  A program that cannot be compiled runs on the
+ * generic kernels.  twofold_ew_jit sets the mode (0 off, 1 automatic, 2 at
+ * every size; -1 only queries), returns the previous one (the initial mode is
+ * $TWOFOLD_JIT when set, else 1), and reports how many kernels were built
+ * and failed so far (either pointer may be NULL).  No paper counterpart. */
+int twofold_ew_jit(int32_t mode, int64_t *built, int64_t *failed);
+
 /* Plain binary64 twin of twofold_ew: the same program on the hi arrays
  * only (in: HOST array of nin device pointers), out[i] = the plain result
  * (a coupled op evaluates as its basic op).  It equals twofold_ew's z0 bit

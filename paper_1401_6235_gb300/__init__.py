@@ -109,6 +109,7 @@ SIGNATURES = {
     "twofold_ew": ([_P, _I32, _P, _I32, _I64, _OUT, _PP, _P], ctypes.c_int),
     "plain_ew": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
     "twofold_ew_f32": ([_P, _I32, _P, _I32, _I64, tf_out_f32, _PP, _P], ctypes.c_int),
+    "twofold_ew_jit": ([_I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
     "plain_ew_f32": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
     "twofold_workspace_bytes": ([_I32, _I64, _I32, _PP], _SZ),
     "twofold_sum": ([_IN, _I64, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
@@ -305,6 +306,17 @@ def plain_ew_f32(prog, his, out=None, stream=None):
     _check(lib().plain_ew_f32(pa.ctypes.data, pa.shape[0], ptrs, len(his), n, _dev(out, "out", True),
                               _stream(stream)), "plain_ew_f32")
     return out
+
+
+def jit_mode(mode: int = -1):
+    """Set the runtime-specialisation mode of the elementwise calls (0 off,
+    1 automatic for n >= 2^20, 2 always; -1 only queries).  Returns
+    (previous mode, kernels built, builds failed)."""
+    b, f = ctypes.c_int64(), ctypes.c_int64()
+    prev = lib().twofold_ew_jit(mode, ctypes.byref(b), ctypes.byref(f))
+    if prev < 0:
+        raise TwofoldError(prev, "twofold_ew_jit")
+    return prev, b.value, f.value
 
 
 def _red_out(njobs, device, out):

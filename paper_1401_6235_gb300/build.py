@@ -19,7 +19,10 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-fmad=false", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
               "-Xptxas", "-v"]
-SOURCES = ["tf_abi.cu", "tf_ew.cu", "tf_reduce.cu", "tf_horner.cu", "tf_batch.cu", "tf_serve.cu"]
+SOURCES = ["tf_abi.cu", "tf_ew.cu", "tf_reduce.cu", "tf_horner.cu", "tf_batch.cu", "tf_serve.cu", "tf_jit.cu"]
+# device headers the runtime compiler of tf_jit.cu gets as text (embedded at build time)
+JIT_HEADERS = ["tf_soft.cuh", "tf_device.cuh", "tf_device_f32.cuh"]
+CUDA_LIB = "/usr/local/cuda/lib64"
 
 
 def nvcc() -> str:
@@ -36,10 +39,29 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _jit_sources(path: str) -> None:
+    """Write the JIT's device headers as C string literals (only when changed)."""
+    parts = ["// generated by build.py from csrc/" + ", csrc/".join(JIT_HEADERS) + "\n",
+             f"static const int kJitHeaderCount = {len(JIT_HEADERS)};\n",
+             "static const char *const kJitHeaderNames[] = {" + ", ".join(f'"{h}"' for h in JIT_HEADERS) + "};\n",
+             "static const char *const kJitHeaders[] = {\n"]
+    for h in JIT_HEADERS:
+        text = open(os.path.join(CSRC, h)).read()
+        assert ")TFJITSRC" not in text
+        parts.append('R"TFJITSRC(' + text + ')TFJITSRC",\n')
+    parts.append("};\n")
+    body = "".join(parts)
+    if not os.path.exists(path) or open(path).read() != body:
+        with open(path, "w") as f:
+            f.write(body)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    _jit_sources(os.path.join(BUILD, "tf_jit_sources.inc"))
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(HERE, "..", "include", "twofold.h"))
+    headers.append(os.path.join(BUILD, "tf_jit_sources.inc"))
     objs = []
     jobs = []
     for src in SOURCES:
@@ -47,7 +69,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc(), *ARCH, *NVCC_FLAGS, "-c", s, "-o", o])
+            jobs.append([nvcc(), *ARCH, *NVCC_FLAGS, "-I", BUILD, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -62,7 +84,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(log)
     if force or jobs or _stale(OUT, objs):
         tmp = OUT + f".tmp{os.getpid()}"
-        run([nvcc(), *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"])
+        run([nvcc(), *ARCH, "-shared", *objs, "-o", tmp, "-lcudart", "-lnvrtc", "-L", CUDA_LIB,
+             "-Xlinker", "-rpath", "-Xlinker", CUDA_LIB])
         os.replace(tmp, OUT)
     return OUT
 

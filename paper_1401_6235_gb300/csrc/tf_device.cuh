@@ -8,7 +8,9 @@
 // function performs the operations of its algorithm in the paper's order, so
 // results are bit-identical to any correct implementation of the sequence.
 #pragma once
+#if !defined(__CUDACC_RTC__)
 #include <cstdint>
+#endif
 
 #include "tf_soft.cuh"
 

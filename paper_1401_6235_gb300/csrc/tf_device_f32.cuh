@@ -8,7 +8,9 @@
 // on this GPU, so the exact transforms are the literal operation sequences.
 // The functions overload the binary64 ones of tf_device.cuh by argument type.
 #pragma once
+#if !defined(__CUDACC_RTC__)
 #include <cstdint>
+#endif
 
 #include "tf_device.cuh"
 

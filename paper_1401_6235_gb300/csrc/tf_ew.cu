@@ -12,6 +12,7 @@
 // per number type and with or without the coupled operations.
 #include "tf_host.cuh"
 #include "tf_device_f32.cuh"
+#include "tf_jit.h"
 
 namespace {
 
@@ -230,6 +231,20 @@ int run_ew(const int32_t *prog, int32_t nprog, const In *in, int32_t nin, int64_
     bool coupled = false;
     for (int q = 0; q < nprog; ++q) coupled |= A.op[q] > TF_SQRT;
     cudaStream_t st = tfh::as_stream(stream);
+    // large arrays: the program's own straight-line kernel (compiled once)
+    tfjit::Prog jp{};
+    jp.nprog = nprog;
+    jp.nin = nin;
+    for (int q = 0; q < nprog; ++q) {
+        jp.op[q] = A.op[q]; jp.dst[q] = A.dst[q]; jp.a[q] = A.a[q]; jp.b[q] = A.b[q];
+    }
+    for (int k = 0; k < nin; ++k)
+        if (!A.lo[k]) jp.dotted_mask |= 1u << k;
+    jp.flags = A.flags != nullptr;
+    jp.sticky = (A.fc.mode & TF_PANIC_STICKY) != 0;
+    jp.is_f32 = sizeof(T) == 4;
+    int jst = TF_OK;
+    if (tfjit::launch(jp, A.hi, A.lo, A.out_hi, A.out_lo, A.flags, A.fc, n, st, &jst)) return jst;
     ChainArgs<T> C{};
     if (as_chain(A.op, A.dst, A.a, A.b, nprog, nin, C)) {
         C.n = n;
@@ -266,6 +281,19 @@ int run_plain(const int32_t *prog, int32_t nprog, const T *const *in, int32_t ni
         A.in[k] = in[k];
     }
     A.n = n; A.nprog = nprog; A.nin = nin; A.out = out;
+    tfjit::Prog jp{};
+    jp.nprog = nprog;
+    jp.nin = nin;
+    for (int q = 0; q < nprog; ++q) {
+        jp.op[q] = A.op[q]; jp.dst[q] = A.dst[q]; jp.a[q] = A.a[q]; jp.b[q] = A.b[q];
+    }
+    jp.dotted_mask = (1u << nin) - 1;
+    jp.is_f32 = sizeof(T) == 4;
+    jp.plain = true;
+    const T *nolo[TF_EW_MAX_INPUTS] = {};
+    typename FlagOf<T>::type fc{};
+    int jst = TF_OK;
+    if (tfjit::launch(jp, A.in, nolo, out, nullptr, nullptr, fc, n, tfh::as_stream(stream), &jst)) return jst;
     const size_t smem = (size_t)A.ntemp * kThreads * sizeof(T);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(plain_ew_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

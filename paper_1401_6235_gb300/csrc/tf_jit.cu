@@ -1,0 +1,268 @@
+// Runtime specialisation of elementwise programs.
+//
+// For large arrays twofold_ew / twofold_ew_f32 compile the program itself
+// into a straight-line kernel: the operations, operand kinds and flag mode
+// become compile-time constants, every input of the thread's elements is
+// loaded before any arithmetic (two elements per thread for the
+// bandwidth-bound binary32 basis), and no per-step dispatch remains; the
+// plain twins are specialised the same way.  The
+// source is generated here, compiled once per distinct program by NVRTC for
+// sm_103a from the same device headers the library is built from (embedded
+// at build time), loaded with cudaLibraryLoadData and cached.  The
+// arithmetic is the library's own device code, so the bits are those of the
+// generic kernels; any failure to build leaves the call on them.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include <nvrtc.h>
+
+#include "tf_host.cuh"
+#include "tf_device_f32.cuh"
+#include "tf_jit.h"
+#include "tf_jit_sources.inc"     // kJitHeaderNames / kJitHeaders: the device headers as text
+
+namespace tfjit {
+namespace {
+
+constexpr int kThreads = 128;
+
+// binary32 is bandwidth-bound: two elements per thread, all loads first;
+// binary64 is bound by its arithmetic: one element per thread, more threads.
+int elems_of(const Prog &p) { return p.is_f32 ? 2 : 1; }
+
+std::mutex g_mu;
+std::unordered_map<std::string, cudaKernel_t> g_cache;     // nullptr: failed to build
+int g_mode = -1;                                            // -1: read TWOFOLD_JIT once
+int64_t g_built = 0, g_failed = 0;
+
+int mode_locked() {
+    if (g_mode < 0) {
+        const char *e = std::getenv("TWOFOLD_JIT");
+        g_mode = e && (e[0] == '0' || e[0] == '2') ? e[0] - '0' : 1;
+    }
+    return g_mode;
+}
+
+std::string key_of(const Prog &p) {
+    std::string k(p.is_f32 ? "f" : "d");
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "|%d|%d|%x|%d|%d|%d|", p.nprog, p.nin, p.dotted_mask, p.flags ? 1 : 0,
+                  p.sticky ? 1 : 0, p.plain ? 1 : 0);
+    k += buf;
+    for (int s = 0; s < p.nprog; ++s) {
+        std::snprintf(buf, sizeof buf, "%d,%d,%d,%d;", p.op[s], p.dst[s], p.a[s], p.b[s]);
+        k += buf;
+    }
+    return k;
+}
+
+bool unary(int op) { return op == TF_SQRT || op == TF_PSQRT; }
+
+// Source of the specialised kernel.
+std::string source_of(const Prog &p) {
+    bool coupled = false, used[TF_EW_MAX_REGS] = {}, written[TF_EW_MAX_REGS] = {};
+    for (int s = 0; s < p.nprog; ++s) {
+        coupled |= p.op[s] > TF_SQRT;
+        used[p.a[s]] = true;
+        if (!unary(p.op[s])) used[p.b[s]] = true;
+        written[p.dst[s]] = true;
+    }
+    const char *T = p.is_f32 ? "float" : "double";
+    const char *pair = p.is_f32 ? "tf::f2" : "tf::d2";
+    std::string s =
+        "typedef unsigned long long uint64_t; typedef long long int64_t; typedef unsigned int uint32_t;\n"
+        "typedef int int32_t; typedef unsigned short uint16_t; typedef unsigned char uint8_t; typedef signed char int8_t;\n"
+        "#include \"tf_device_f32.cuh\"\n";
+    s += std::string("typedef ") + T + " T;\n";
+    s += std::string("typedef ") + (p.is_f32 ? "tf::FlagCfg32" : "tf::FlagCfg") + " FC;\n";
+    s += "struct JArgs { long long n; const T *hi[12]; const T *lo[12]; T *oh; T *ol; unsigned char *fl; FC fc; };\n";
+    const int E = elems_of(p);
+    s += std::string("extern \"C\" __global__ void __launch_bounds__(128") + (p.is_f32 ? "" : ", 12") +
+         ") tf_jit_ew(const __grid_constant__ JArgs A) {\n";
+    s += "  for (long long i0 = (long long)blockIdx.x * " + std::to_string(128 * E) +
+         " + threadIdx.x; i0 < A.n; i0 += (long long)gridDim.x * " + std::to_string(128 * E) + ") {\n";
+    if (E == 2) s += "    const long long i1 = i0 + 128; const bool v1 = i1 < A.n;\n";
+    char buf[512];
+    // all loads first, every element of the thread
+    for (int e = 0; e < E; ++e) {
+        for (int k = 0; k < p.nin; ++k) {
+            if (!used[k]) continue;
+            const std::string r = "e" + std::to_string(e) + "r" + std::to_string(k), ks = std::to_string(k);
+            const bool dotted = p.plain || ((p.dotted_mask >> k) & 1);
+            if (e == 0) {
+                s += "    T " + r + "_0 = A.hi[" + ks + "][i0];";
+                s += " T " + r + "_1 = " + (dotted ? std::string("T(0)") : "A.lo[" + ks + "][i0]") + ";\n";
+            } else {
+                s += "    T " + r + "_0 = v1 ? A.hi[" + ks + "][i1] : T(1);";
+                s += " T " + r + "_1 = " + (dotted ? std::string("T(0)") : "v1 ? A.lo[" + ks + "][i1] : T(0)") + ";\n";
+            }
+        }
+    }
+    for (int e = 0; e < E; ++e) {
+        s += "    {\n      unsigned char st = 0;\n";
+        for (int r = p.nin; r < TF_EW_MAX_REGS; ++r)
+            if (written[r]) {
+                std::snprintf(buf, sizeof buf, "      T e%dr%d_0, e%dr%d_1;\n", e, r, e, r);
+                s += buf;
+            }
+        for (int q = 0; q < p.nprog; ++q) {
+            const int op = p.op[q], a = p.a[q], b = p.b[q], d = p.dst[q];
+            if (p.plain) {                       // the plain twin: heads only
+                std::snprintf(buf, sizeof buf, "      e%dr%d_0 = tf::apply_plain(%d, e%dr%d_0, %s);\n", e, d, op, e, a,
+                              unary(op) ? "T(0)" : ("e" + std::to_string(e) + "r" + std::to_string(b) + "_0").c_str());
+                s += buf;
+                continue;
+            }
+            const bool xd = a < p.nin && ((p.dotted_mask >> a) & 1);
+            const bool yd = unary(op) || (b < p.nin && ((p.dotted_mask >> b) & 1));
+            std::string y0 = "T(0)", y1 = "T(0)";
+            if (!unary(op)) {
+                y0 = "e" + std::to_string(e) + "r" + std::to_string(b) + "_0";
+                y1 = "e" + std::to_string(e) + "r" + std::to_string(b) + "_1";
+            }
+            std::snprintf(buf, sizeof buf,
+                          "      { const %s z = tf::apply_any<%s>(%d, e%dr%d_0, e%dr%d_1, %s, %s, %s, %s); "
+                          "e%dr%d_0 = z.z0; e%dr%d_1 = z.z1;%s }\n",
+                          pair, coupled ? "true" : "false", op, e, a, e, a, xd ? "true" : "false", y0.c_str(),
+                          y1.c_str(), yd ? "true" : "false", e, d, e, d,
+                          p.sticky ? " st |= tf::flag_of(z.z0, z.z1, A.fc);" : "");
+            s += buf;
+        }
+        const int last = p.dst[p.nprog - 1];
+        const char *idx = e == 0 ? "i0" : "i1";
+        if (p.plain) std::snprintf(buf, sizeof buf, "      %sA.oh[%s] = e%dr%d_0;\n", e == 0 ? "" : "if (v1) ", idx, e, last);
+        else std::snprintf(buf, sizeof buf, "      %s{ A.oh[%s] = e%dr%d_0; A.ol[%s] = e%dr%d_1; }\n",
+                           e == 0 ? "" : "if (v1) ", idx, e, last, idx, e, last);
+        s += buf;
+        if (p.flags && !p.plain) {
+            std::snprintf(buf, sizeof buf, "      %sA.fl[%s] = tf::flag_of(e%dr%d_0, e%dr%d_1, A.fc) | st;\n",
+                          e == 0 ? "" : "if (v1) ", idx, e, last, e, last);
+            s += buf;
+        }
+        s += "      (void)st;\n    }\n";
+    }
+    s += "  }\n}\n";
+    return s;
+}
+
+cudaKernel_t build(const Prog &p) {
+    const std::string src = source_of(p);
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, src.c_str(), "tf_jit_ew.cu", kJitHeaderCount, kJitHeaders, kJitHeaderNames) !=
+        NVRTC_SUCCESS)
+        return nullptr;
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "--fmad=false", "-default-device",
+                          "--ftz=false", "--prec-div=true", "--prec-sqrt=true"};
+    const nvrtcResult cr = nvrtcCompileProgram(prog, (int)(sizeof opts / sizeof opts[0]), opts);
+    size_t n = 0;
+    std::string cubin;
+    if (cr == NVRTC_SUCCESS && nvrtcGetCUBINSize(prog, &n) == NVRTC_SUCCESS && n > 0) {
+        cubin.resize(n);
+        if (nvrtcGetCUBIN(prog, &cubin[0]) != NVRTC_SUCCESS) cubin.clear();
+    } else if (std::getenv("TWOFOLD_JIT_LOG")) {
+        size_t ln = 0;
+        nvrtcGetProgramLogSize(prog, &ln);
+        std::string log(ln, '\0');
+        nvrtcGetProgramLog(prog, &log[0]);
+        std::fprintf(stderr, "twofold JIT: compile failed\n%s\n%s\n", src.c_str(), log.c_str());
+    }
+    nvrtcDestroyProgram(&prog);
+    if (cubin.empty()) return nullptr;
+    cudaLibrary_t lib;
+    const cudaError_t le = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (le != cudaSuccess) {
+        if (std::getenv("TWOFOLD_JIT_LOG"))
+            std::fprintf(stderr, "twofold JIT: %zu-byte cubin not loaded: %s\n", cubin.size(), cudaGetErrorString(le));
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    cudaKernel_t k;
+    if (cudaLibraryGetKernel(&k, lib, "tf_jit_ew") != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return k;
+}
+
+template <typename T, typename FC>
+struct JArgs {
+    long long n;
+    const T *hi[12];
+    const T *lo[12];
+    T *oh, *ol;
+    unsigned char *fl;
+    FC fc;
+};
+
+template <typename T, typename FC>
+bool launch_impl(const Prog &p, const T *const *hi, const T *const *lo, T *oh, T *ol, uint8_t *fl, const FC &fc,
+                 int64_t n, cudaStream_t stream, int *status) {
+    cudaKernel_t k;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        const int m = mode_locked();
+        if (m == 0 || (m == 1 && n < kAutoMinElements)) return false;
+        const std::string key = key_of(p);
+        auto it = g_cache.find(key);
+        if (it == g_cache.end()) {
+            k = build(p);
+            g_cache.emplace(key, k);
+            if (k) ++g_built;
+            else ++g_failed;
+        } else {
+            k = it->second;
+        }
+    }
+    if (!k) return false;
+    JArgs<T, FC> A{};
+    A.n = n;
+    for (int i = 0; i < p.nin; ++i) {
+        A.hi[i] = hi[i];
+        A.lo[i] = lo[i];
+    }
+    A.oh = oh;
+    A.ol = ol;
+    A.fl = fl;
+    A.fc = fc;
+    const int64_t want = (n + kThreads * elems_of(p) - 1) / (kThreads * elems_of(p));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k, kThreads, 0) != cudaSuccess ||
+        per_sm < 1) {
+        (void)cudaGetLastError();
+        per_sm = 8;
+    }
+    const int64_t cap = (int64_t)tfh::sm_count() * per_sm;
+    void *args[] = {&A};
+    const cudaError_t e =
+        cudaLaunchKernel((const void *)k, dim3((unsigned)(want < cap ? want : cap)), dim3(kThreads), args, 0, stream);
+    *status = e == cudaSuccess ? TF_OK : TF_ECUDA;
+    return true;
+}
+
+}  // namespace
+
+bool launch(const Prog &p, const double *const *hi, const double *const *lo, double *oh, double *ol, uint8_t *fl,
+            const tf::FlagCfg &fc, int64_t n, cudaStream_t stream, int *status) {
+    return launch_impl(p, hi, lo, oh, ol, fl, fc, n, stream, status);
+}
+
+bool launch(const Prog &p, const float *const *hi, const float *const *lo, float *oh, float *ol, uint8_t *fl,
+            const tf::FlagCfg32 &fc, int64_t n, cudaStream_t stream, int *status) {
+    return launch_impl(p, hi, lo, oh, ol, fl, fc, n, stream, status);
+}
+
+}  // namespace tfjit
+
+extern "C" int twofold_ew_jit(int32_t mode, int64_t *built, int64_t *failed) {
+    std::lock_guard<std::mutex> g(tfjit::g_mu);
+    const int prev = tfjit::mode_locked();
+    if (mode >= 0 && mode <= 2) tfjit::g_mode = mode;
+    else if (mode != -1) return TF_EINVAL;
+    if (built) *built = tfjit::g_built;
+    if (failed) *failed = tfjit::g_failed;
+    return prev;
+}

@@ -25,9 +25,11 @@
 // check the integer algorithms against the CPU's IEEE operations; there the
 // seeds come from correctly rounded float operations.
 #pragma once
+#if !defined(__CUDACC_RTC__)   // the runtime compiler gets the integer types from its prelude
 #include <cstdint>
 #include <cstring>
 #include <cmath>
+#endif
 
 #if defined(__CUDACC__)
 #define TFS_HD __host__ __device__ __forceinline__
