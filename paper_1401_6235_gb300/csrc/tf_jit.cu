@@ -82,7 +82,7 @@ std::string source_of(const Prog &p) {
     s += "struct JArgs { long long n; const T *hi[12]; const T *lo[12]; T *oh; T *ol; unsigned char *fl; FC fc; };\n";
     const int E = elems_of(p);
     s += std::string("extern \"C\" __global__ void __launch_bounds__(128") + (p.is_f32 ? "" : ", 12") +
-         ") tf_jit_ew(const __grid_constant__ JArgs A) {\n";
+         ") " + (p.plain ? "tf_jit_plain" : "tf_jit_ew") + "(const __grid_constant__ JArgs A) {\n";
     s += "  for (long long i0 = (long long)blockIdx.x * " + std::to_string(128 * E) +
          " + threadIdx.x; i0 < A.n; i0 += (long long)gridDim.x * " + std::to_string(128 * E) + ") {\n";
     if (E == 2) s += "    const long long i1 = i0 + 128; const bool v1 = i1 < A.n;\n";
@@ -181,7 +181,7 @@ cudaKernel_t build(const Prog &p) {
         return nullptr;
     }
     cudaKernel_t k;
-    if (cudaLibraryGetKernel(&k, lib, "tf_jit_ew") != cudaSuccess) {
+    if (cudaLibraryGetKernel(&k, lib, p.plain ? "tf_jit_plain" : "tf_jit_ew") != cudaSuccess) {
         (void)cudaGetLastError();
         return nullptr;
     }
