@@ -153,10 +153,8 @@ def time_steps(step, steps, warmup, dist_on):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     if dist_on:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_1401_6235_gb300.dist import max_over_ranks
+        ms = max_over_ranks(ms, device="cuda")
     return ms
 
 

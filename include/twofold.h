@@ -255,6 +255,17 @@ int plain_dot(const double *x, const double *y, int64_t n, double *out1, const t
 int plain_dot_batched(const double *x, const double *y, const int64_t *offs, int32_t njobs,
                       double *out, const tf_params *p, void *ws, size_t ws_bytes, void *stream);
 
+/* The upper levels of the reduction order over m partial results (z0[i],
+ * z1[i] device arrays): the pairwise tree with the odd node carried, then
+ * the panic flag, as a sum or dot ends.  When the partials are the results
+ * of consecutive aligned blocks of 2^k leaves of one sum or dot (for
+ * example one block per GPU of a sharded reduction), the result is the
+ * whole reduction's, bit for bit.  m == 0 gives (+0, +0).  ws_bytes >=
+ * 2 * 256-rounded 8m bytes (the partials are copied there first; the inputs
+ * are not modified).  No paper counterpart: the multi-GPU split's combine. */
+int twofold_combine(const double *z0, const double *z1, int64_t m, tf_out out1, const tf_params *p,
+                    void *ws, size_t ws_bytes, void *stream);
+
 /* Dot product that allocates nothing and takes no workspace (the paper has
  * no counterpart: this is an interface for callers that cannot provide
  * device memory at the call, e.g. code that must not touch the allocator

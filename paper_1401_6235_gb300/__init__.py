@@ -120,6 +120,7 @@ SIGNATURES = {
     "plain_dot": ([_P, _P, _I64, _P, _PP, _P, _SZ, _P], ctypes.c_int),
     "plain_dot_batched": ([_P, _P, _P, _I32, _P, _PP, _P, _SZ, _P], ctypes.c_int),
     "twofold_dot_noalloc": ([_IN, _IN, _I64, _OUT, _PP, _P], ctypes.c_int),
+    "twofold_combine": ([_P, _P, _I64, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
     "twofold_horner": ([_P, _I32, _P, _I64, _OUT, _PP, _P], ctypes.c_int),
     "twofold_horner_workspace_bytes": ([_I32], _SZ),
     "twofold_horner_batched": ([_P, _P, _P, _I32, _P, _P, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
@@ -345,6 +346,19 @@ def twofold_dot(x, y, xl=None, yl=None, out=None, p: tf_params | None = None, ws
     _check(lib().twofold_dot(tf_in(_dev(x), _dev(xl)), tf_in(_dev(y), _dev(yl)), n,
                              tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws), ws.numel(),
                              _stream(stream)), "twofold_dot")
+    return hi, lo, fl
+
+
+def twofold_combine(z0, z1, out=None, p: tf_params | None = None, ws=None, stream=None):
+    """The pairwise tree over partial results (device float64 tensors of the
+    same length): the end of a sum or dot split into aligned 2^k-leaf blocks."""
+    m = z0.numel()
+    if z1.numel() != m:
+        raise ValueError("z0 and z1 must have the same length")
+    ws = workspace(max(256, 2 * ((8 * m + 255) // 256 * 256))) if ws is None else ws
+    hi, lo, fl = _red_out(1, z0.device, out)
+    _check(lib().twofold_combine(_dev(z0), _dev(z1), m, tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws),
+                                 ws.numel(), _stream(stream)), "twofold_combine")
     return hi, lo, fl
 
 

@@ -44,6 +44,7 @@ struct RedArgs {
     double *out_hi, *out_lo;
     uint8_t *flags;
     tf::FlagCfg fc;
+    int write_single;          // reduce_final writes jobs of one partial too (twofold_combine)
 };
 
 // Job of block b: the largest j with blk0[j] <= b (empty jobs own no block).
@@ -421,7 +422,10 @@ __global__ void __launch_bounds__(kThreads) reduce_final(const __grid_constant__
     griddep_release();
     const int j = blockIdx.x, t = threadIdx.x;
     const int64_t p0 = A.tab.b0(j), nb = A.tab.b0(j + 1) - p0;
-    if (nb == 1) return;
+    if (nb == 1) {
+        if (A.write_single && t == 0) write_result<PLAIN>(A, j, {A.part0[p0], A.part1[p0]});
+        return;
+    }
     if (nb == 0) {
         if (t == 0) write_result<PLAIN>(A, j, {0.0, 0.0});
         return;
@@ -688,4 +692,37 @@ extern "C" int twofold_dot_noalloc(tf_in x, tf_in y, int64_t n, tf_out out1, con
     const int r = run<true, false>(x.hi, x.lo, y.hi, y.lo, offs, 1, out1.hi, out1.lo, out1.flags, p, scratch,
                                    kNoAllocScratchBytes, stream);
     return r == TF_ENOSPC ? TF_EUNSUPPORTED : r;     // beyond the static scratch
+}
+
+// The upper levels of the blocked pairwise order over m partials given in
+// device memory (the results of aligned 2^k-leaf blocks, e.g. one per
+// shard): the pairwise tree with the odd node carried, then the flag.
+extern "C" int twofold_combine(const double *z0, const double *z1, int64_t m, tf_out out1, const tf_params *p,
+                               void *ws, size_t ws_bytes, void *stream) {
+    if (m < 0 || !tfh::params_ok(p) || !tfh::dptr_ok(out1.hi) || !tfh::dptr_ok(out1.lo)) return TF_EINVAL;
+    if (m > 0 && (!tfh::dptr_ok(z0) || !tfh::dptr_ok(z1))) return TF_EINVAL;
+    const size_t need = 2 * align256(sizeof(double) * (size_t)m);
+    if (m > 0 && (!ws || ws_bytes < need || !tfh::aligned8(ws))) return TF_ENOSPC;
+    RedArgs A{};
+    A.njobs = 1;
+    A.tab.ioffs[0] = 0;
+    A.tab.ioffs[1] = m;
+    A.tab.iblk0[0] = 0;
+    A.tab.iblk0[1] = m;
+    A.out_hi = out1.hi;
+    A.out_lo = out1.lo;
+    A.flags = out1.flags;
+    A.fc = tfh::flag_cfg(p);
+    A.write_single = 1;
+    cudaStream_t s = tfh::as_stream(stream);
+    if (m > 0) {
+        // the tree works in place: on a copy in the workspace
+        A.part0 = static_cast<double *>(ws);
+        A.part1 = reinterpret_cast<double *>(static_cast<char *>(ws) + align256(sizeof(double) * (size_t)m));
+        if (cudaMemcpyAsync(A.part0, z0, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(A.part1, z1, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return TF_ECUDA;
+    }
+    if (tfh::launch_pdl(reduce_final<false>, 1, kThreads, 0, s, A) != cudaSuccess) return TF_ECUDA;
+    return tfh::launch_status();
 }

@@ -104,6 +104,21 @@ def test_reduce_rejects_bad_offsets_and_small_workspace(L):
     assert L.twofold_sum(x, -5, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
 
 
+def test_combine_rejects_bad_arguments(L):
+    """Every case fails validation before any copy or launch."""
+    out = T.tf_out(FAKE, FAKE, None)
+    assert L.twofold_combine(FAKE, FAKE, -1, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_combine(FAKE, FAKE, 4, T.tf_out(None, FAKE, None), None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_combine(FAKE, FAKE, 4, T.tf_out(FAKE, FAKE + 4, None), None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_combine(None, FAKE, 4, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_combine(FAKE, FAKE + 2, 4, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    bad = T.params(panic_mode=7)
+    assert L.twofold_combine(FAKE, FAKE, 4, out, ctypes.byref(bad), FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_combine(FAKE, FAKE, 40, out, None, FAKE, 2 * 256 - 8, None) == T.TF_ENOSPC
+    assert L.twofold_combine(FAKE, FAKE, 40, out, None, None, 1 << 20, None) == T.TF_ENOSPC
+    assert L.twofold_combine(FAKE, FAKE, 40, out, None, FAKE + 4, 1 << 20, None) == T.TF_ENOSPC
+
+
 def test_workspace_bound_covers_every_split(L):
     """The workspace query is an upper bound of what the call needs for any
     job mix with that total length (host arithmetic only)."""
