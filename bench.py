@@ -158,6 +158,34 @@ def time_steps(step, steps, warmup, dist_on):
     return ms
 
 
+def graph_throughput(call, reps):
+    """`reps` back-to-back calls captured in one CUDA graph, replayed 3 times:
+    mean microseconds per call and calls per second (launch cost removed)."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            call()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            call()
+    g.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / (3 * reps)
+    return {"calls_in_graph": reps, "replays": 3, "us_per_call": us, "calls_per_s": 1e6 / us}
+
+
 # --------------------------------------------------------------- workloads
 
 def workload_ew(args, rank, world, dist_on):
@@ -265,6 +293,7 @@ def workload_dot(args, rank, world, dist_on):
         hres[1:2].copy_(out[1], non_blocking=True)
 
     e2e_ms = time_steps(e2e_step, args.steps, args.warmup, dist_on)
+    graph = graph_throughput(lambda: T.twofold_dot(gx, gy, out=out, ws=ws), 1000)
     per = ms / args.steps
     return {
         "metric": "twofold dot latency (n=65536)", "value": per * 1e3, "unit": "us",
@@ -276,6 +305,7 @@ def workload_dot(args, rank, world, dist_on):
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_ms / args.steps * 1e3, "unit": "us", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 16},
+        "graph": graph,
         "gpu_launches": 2 * args.steps, "clocks": cs.summary(),    # leaves kernel + final tree
         "_kernel_ms": per, "_ops": DOT_OPS * n, "_bytes": DOT_BYTES * n, "_units": n,
         "_sample": lambda: cpu_sample_dot(n),
@@ -441,33 +471,43 @@ def workload_batch_mix(args, rank, world, dist_on):
 
 def workload_serve(args, rank, world, dist_on):
     """A Poisson stream of mixed requests (dot 40 %, sum 20 %, Horner k 8-30
-    20 %, elementwise chain 20 %; sizes 10^U(3,6)) through the request server
-    at several arrival rates: achieved jobs/s and p50 / p99 latency from
-    submission to completion, against a one-worker server that runs each
-    request alone (copy in, single-job call, copy out, synchronise) on the
-    same arrival times (its queue is replayed from measured service times)."""
+    20 %, elementwise chain 20 %; sizes 10^U(3,7); dots of condition
+    10^U(0,20)) through the request server at several arrival rates:
+    achieved jobs/s and p50 / p99 latency from submission to completion,
+    against a one-worker server that runs each request alone (copy in,
+    single-job call, copy out, synchronise) on the same arrival times (its
+    queue is replayed from measured service times)."""
     import torch
     import paper_1401_6235_gb300 as T
     from paper_1401_6235_gb300.serve import Server
     import synth
     rng = np.random.default_rng(2000 + rank)
-    nreq = args.n or 3000
-    rates = [4000.0, 16000.0, 64000.0]
-    pool = 1 << 21
+    nreq = args.n or 100000
+    rates = [2000.0, 4000.0, 8000.0, 16000.0]
+    per_rate = [min(nreq, int(8 * r)) for r in rates[:-1]] + [nreq]    # ~8 s of arrivals below the top rate
+    pool = 1 << 24
     pin = lambda m: torch.empty(m, dtype=torch.float64).pin_memory().numpy()
-    xy = synth.ew_chain(pool, seed=rank, pinned=pin)              # 8 pinned pools of 2^21 doubles
+    xy = synth.ew_chain(pool, seed=rank, pinned=pin)              # 8 pinned pools of 2^24 doubles
     hx = synth.horner_points(pool, seed=rank, stream=5)
     coef = {k: synth.binomial_coefs(k) for k in range(8, 31)}
     kinds = rng.choice(["dot", "sum", "horner", "ew"], size=nreq, p=[0.4, 0.2, 0.2, 0.2])
-    sizes = np.floor(10.0 ** rng.uniform(3, 6, nreq)).astype(np.int64)
+    sizes = np.floor(10.0 ** rng.uniform(3, 7, nreq)).astype(np.int64)
     offs = (rng.random(nreq) * (pool - sizes)).astype(np.int64)
     degs = rng.integers(8, 31, nreq)
+    # dot requests: one of 128 ill-conditioned dots built up front (sizes 10^U(3,7), conditions 10^U(0,20))
+    ndots = 128
+    dsz = np.floor(10.0 ** rng.uniform(3, 7, ndots)).astype(np.int64)
+    dx, dy = pin(int(dsz.sum())), pin(int(dsz.sum()))
+    _, _, doffs, _, dcond = synth.cond_dots_sized(dsz, 10.0 ** rng.uniform(0, 20, ndots), seed=7 + rank, x=dx, y=dy)
+    dsel = rng.integers(0, ndots, nreq)
+    sizes = np.where(kinds == "dot", dsz[dsel], sizes)
 
     def args_of(i):
         a, n = int(offs[i]), int(sizes[i])
         sl = slice(a, a + n)
         if kinds[i] == "dot":
-            return ("dot", xy["a0"][sl], xy["b0"][sl])
+            d = slice(int(doffs[dsel[i]]), int(doffs[dsel[i] + 1]))
+            return ("dot", dx[d], dy[d])
         if kinds[i] == "sum":
             return ("sum", xy["c0"][sl])
         if kinds[i] == "horner":
@@ -510,12 +550,12 @@ def workload_serve(args, rank, world, dist_on):
         for q in structs[:50]:                       # warm the server, the allocator and the kernels
             submit_c(h, ctypes.byref(q), ctypes.byref(tid))
             wait_c(h, tid.value, -1, ctypes.byref(info))
-        for rate in rates:
-            arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        for rate, nr in zip(rates, per_rate):
+            arrive = np.cumsum(rng.exponential(1.0 / rate, nr))
             arrivals.append(arrive)
-            ids = np.empty(nreq, np.uint64)
+            ids = np.empty(nr, np.uint64)
             t0 = time.perf_counter()
-            for i, q in enumerate(structs):
+            for i, q in enumerate(structs[:nr]):
                 while time.perf_counter() - t0 < arrive[i]:
                     pass
                 st_ = submit_c(h, ctypes.byref(q), ctypes.byref(tid))
@@ -523,14 +563,14 @@ def workload_serve(args, rank, world, dist_on):
                     raise RuntimeError(f"submit: {T.strerror(st_)}")
                 ids[i] = tid.value
             sub_s = time.perf_counter() - t0
-            rec = np.empty((nreq, 3))
-            for i in range(nreq):
+            rec = np.empty((nr, 3))
+            for i in range(nr):
                 if wait_c(h, int(ids[i]), -1, ctypes.byref(info)) != 0:
                     raise RuntimeError("request failed")
                 rec[i] = (info.submitted_ns, info.done_ns, info.batch_jobs)
             lat = (rec[:, 1] - rec[:, 0]) * 1e-6
             span = (rec[:, 1].max() - rec[:, 0].min()) * 1e-9
-            sweep.append({"rate": rate, "offered_jobs_s": nreq / sub_s, "jobs_s": nreq / span,
+            sweep.append({"rate": rate, "requests": nr, "offered_jobs_s": nr / sub_s, "jobs_s": nr / span,
                           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                           "mean_batch": float(rec[:, 2].mean())})
         stats = srv.stats()
@@ -555,13 +595,14 @@ def workload_serve(args, rank, world, dist_on):
         torch.cuda.synchronize()
         service[i] = time.perf_counter() - t
     for row, arrive in zip(sweep, arrivals):       # the per-job server on the same arrival times
-        done = np.empty(nreq)
+        nr = arrive.size
+        done = np.empty(nr)
         free = 0.0
-        for i in range(nreq):
+        for i in range(nr):
             free = max(arrive[i], free) + service[i]
             done[i] = free
         lat = (done - arrive) * 1e3
-        row["per_job"] = {"jobs_s": nreq / (done[-1] - arrive[0]), "p50_ms": float(np.percentile(lat, 50)),
+        row["per_job"] = {"jobs_s": nr / (done[-1] - arrive[0]), "p50_ms": float(np.percentile(lat, 50)),
                           "p99_ms": float(np.percentile(lat, 99))}
     top = sweep[-1]
     moved = sum(16 * int(sizes[i]) if kinds[i] == "dot" else 8 * int(sizes[i]) if kinds[i] == "sum" else
@@ -570,10 +611,11 @@ def workload_serve(args, rank, world, dist_on):
         "metric": "served twofold jobs/s at the highest offered rate (Poisson, mixed kinds), p50/p99 latency",
         "value": top["jobs_s"], "unit": "jobs/s", "ms_per_step": 1e3 / top["jobs_s"],
         "sweep": sweep, "server": {k: stats[k] for k in ("batches", "batched_jobs", "peak_bytes", "max_inflight")},
-        "config": {"workload": f"{nreq} requests per rate: dot 40%, sum 20%, Horner k 8-30 20%, chain 20%; sizes "
-                               "10^U(3,6) (the 10^7 end of the stated range scaled down so that a run's host "
-                               "traffic stays within a minute); inputs slices of pinned host pools; memory cap 32 GiB",
-                   "rates": rates, "parallelism": f"replicas x{world}"},
+        "config": {"workload": f"Poisson streams of {per_rate} requests (one per rate): dot 40%, sum 20%, Horner k "
+                               "8-30 20%, chain 20%; sizes 10^U(3,7); dots drawn from 128 ill-conditioned dots "
+                               "(cond 10^U(0,20)); other inputs slices of pinned host pools; memory cap 32 GiB",
+                   "rates": rates, "dot_cond_range": [float(dcond.min()), float(dcond.max())],
+                   "parallelism": f"replicas x{world}"},
         "e2e": {"value": top["jobs_s"], "unit": "jobs/s", "h2d_bytes_per_step": int(moved / nreq),
                 "d2h_bytes_per_step": None},
         "gpu_launches": None, "clocks": {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0},

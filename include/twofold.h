@@ -389,7 +389,9 @@ int twofold_batch(const tf_job *jobs, int32_t njobs, const tf_params *p, const t
  * starts one scheduler thread.  Requests carry HOST buffers; they wait in
  * FIFO order, and whenever memory and a stream are free the scheduler admits
  * the longest prefix of the queue that fits the arena (inputs, outputs and
- * the batch workspace), up to max_batch_jobs requests, copies the inputs in,
+ * the batch workspace), up to max_batch_jobs requests and a quarter of
+ * mem_cap_bytes of request buffers (a larger single request is admitted
+ * alone), copies the inputs in,
  * runs the sum / dot / Horner requests as one mixed persistent batch
  * (twofold_batch, with `cfg`) and the elementwise requests as twofold_ew
  * launches, copies the results out and releases the memory when the batch's

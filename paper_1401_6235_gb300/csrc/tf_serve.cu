@@ -5,7 +5,9 @@
 // One scheduler thread per server owns a device arena of the configured
 // size.  Requests wait in FIFO order; whenever memory and a stream are free
 // the scheduler admits the longest prefix of the queue that fits (inputs,
-// outputs and the batch workspace), copies the inputs in, runs the batch and
+// outputs and the batch workspace) within a quarter of the arena (so that
+// up to three batches share it and their copies pipeline even when the
+// queue is long), copies the inputs in, runs the batch and
 // copies the results out on a free stream of its pool, and records an event.
 // Finished batches release their memory, and requests that arrived while
 // others ran are admitted as memory frees up, so several batches are in
@@ -176,6 +178,7 @@ struct tf_server {
     bool stop = false;
     int device = 0;
     int max_jobs = 4096;
+    size_t batch_cap = 0;      // request bytes per batch (a larger single request runs alone)
     bool has_p = false, has_cfg = false;
     tf_params p{};
     tf_batch_config cfg{};
@@ -193,10 +196,13 @@ struct tf_server {
 bool tf_server::admit(Batch &b) {
     const tf_params *pp = has_p ? &p : nullptr;
     const tf_batch_config *cp = has_cfg ? &cfg : nullptr;
+    size_t bytes = 0;
     while (!pending.empty() && (int)b.reqs.size() < max_jobs) {
         auto q = pending.front();
+        if (!b.reqs.empty() && bytes + q->bytes > batch_cap) break;
         size_t off;
         if (!arena.alloc(q->bytes, &off)) break;
+        bytes += q->bytes;
         q->off = off;
         pending.pop_front();
         b.reqs.push_back(q);
@@ -400,6 +406,7 @@ extern "C" int twofold_server_create(size_t mem_cap_bytes, int32_t max_batch_job
         }
     }
     s->max_jobs = max_batch_jobs;
+    s->batch_cap = mem_cap_bytes / kStreams;
     if (p) { s->p = *p; s->has_p = true; }
     if (cfg) { s->cfg = *cfg; s->has_cfg = true; }
     s->st.arena_bytes = (int64_t)mem_cap_bytes;

@@ -182,6 +182,31 @@ def cond_dots(njobs: int = 4096, n: int = 1 << 16, seed: int = 0, e_lo: float = 
     return x, y, offs, exact, cond, targets
 
 
+def cond_dots_sized(sizes, conds, seed: int = 0, x=None, y=None):
+    """Dots of the given lengths and target conditions laid end to end (dot j
+    built from seed ``seed * 2^20 + j``): x, y, offsets, exact dots, realised
+    conditions.  ``x``/``y``: optional output buffers (e.g. pinned memory)."""
+    sizes = np.asarray(sizes, np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    x = np.empty(int(offs[-1]), np.float64) if x is None else x
+    y = np.empty(int(offs[-1]), np.float64) if y is None else y
+    exact = np.empty(sizes.size)
+    cond = np.empty(sizes.size)
+    L = lib()
+
+    def one(j):
+        d = ctypes.c_double()
+        c = ctypes.c_double()
+        L.synth_cond_dot((seed << 20) + j, int(sizes[j]), float(conds[j]), _ptr(x) + 8 * int(offs[j]),
+                         _ptr(y) + 8 * int(offs[j]), ctypes.byref(d), ctypes.byref(c))
+        exact[j] = d.value
+        cond[j] = c.value
+
+    with ThreadPoolExecutor(_THREADS) as ex:
+        list(ex.map(one, range(sizes.size)))
+    return x, y, offs, exact, cond
+
+
 def binomial_coefs(k: int) -> np.ndarray:
     """Ascending coefficients a_0..a_k of (x-1)^k; exact in binary64 for k <= 30."""
     return np.array([math.comb(k, i) * (-1) ** (k - i) for i in range(k + 1)], np.float64)

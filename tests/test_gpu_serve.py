@@ -153,6 +153,20 @@ def test_admission_by_memory():
         assert_bits(z[1], [e1], "z1")
 
 
+def test_batches_stay_within_a_quarter_of_the_arena():
+    """A long queue of 1 MiB requests in a 64 MiB arena: no batch takes more
+    than 16 MiB of request buffers, so several batches are in flight."""
+    xs = [np.full(1 << 17, float(i)) for i in range(200)]
+    with Server(mem_cap=64 << 20, max_batch_jobs=4096) as srv:
+        ts = [srv.submit_sum(x) for x in xs]
+        res = [srv.wait(t) for t in ts]
+        st = srv.stats()
+    assert max(t.info.batch_jobs for t in ts) <= 15
+    assert st["completed"] == 200
+    for i, z in enumerate(res):
+        assert z[0][0] == float(i) * (1 << 17) and z[1][0] == 0.0
+
+
 def test_wait_rejects_unknown_ticket():
     with Server(mem_cap=1 << 20) as srv:
         t = srv.submit_sum(np.ones(10))
