@@ -250,9 +250,27 @@ __device__ __forceinline__ int lat_chunk_start(int c, int n8) {
     return min(n8, first + (c - 1) * per);
 }
 
+// Shared-memory rows of reduce_lat for leaves of length L (rows hold L8 =
+// L rounded up to 8 entries plus padding, so that a chain reads whole
+// blocks of 8 without bounds checks and 16-byte loads of different lanes
+// fall in different banks):
+//   PT [B][L8 + 2]  doubles   p_i (terms; x_i for a sum)
+//   ET [B][L8 + 1]  double2   (e_i, t_i): term tails and Two-Sum tails
+//   CK [B][L8/8 + 1] doubles  z0 checkpoints s_{8k+7}
+// Entries past the end of a leaf hold -0.0, which leaves an accumulator
+// unchanged.
+struct LatRows {
+    int L8, SP, SE, SC;
+    __host__ __device__ explicit LatRows(int64_t L)
+        : L8((int)((L + 7) & ~7)), SP(L8 + 2), SE(L8 + 1), SC(L8 / 8 + 1) {}
+    __host__ __device__ size_t bytes(int B) const {
+        return ((size_t)B * SP + 2 * (size_t)B * SE + (size_t)B * SC) * sizeof(double);
+    }
+};
+
 template <bool DOT, bool PLAIN>
 __global__ void __launch_bounds__(kLatThreads) reduce_lat(const __grid_constant__ RedArgs A) {
-    extern __shared__ double lat[];                  // PT, E : [B][L + 1]; CK : [B][L / 8 + 1]
+    extern __shared__ __align__(16) double lat[];
     __shared__ double r0[32];
     griddep_wait();
     griddep_release();
@@ -264,9 +282,12 @@ __global__ void __launch_bounds__(kLatThreads) reduce_lat(const __grid_constant_
     const int64_t leaf0 = (b - A.tab.b0(j)) * A.B;
     const int nl = (int)min((int64_t)A.B, m - leaf0);
     const int64_t base = e0 + leaf0 * A.L, end = e0 + len;
-    const int L = (int)A.L, Sd = L + 1, Cd = L / 8 + 1;
+    const int L = (int)A.L;
+    const LatRows R(A.L);
     const int nel = (int)min((int64_t)nl * L, end - base);   // elements of the block
-    double *PT = lat, *E = lat + (size_t)A.B * Sd, *CK = lat + 2 * (size_t)A.B * Sd;
+    double *PT = lat;
+    double2 *ET = reinterpret_cast<double2 *>(lat + (size_t)A.B * R.SP);
+    double *CK = lat + (size_t)A.B * R.SP + 2 * (size_t)A.B * R.SE;
     const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
     {
         // element k of the block is element k - r L of leaf r = k / L
@@ -289,51 +310,65 @@ __global__ void __launch_bounds__(kLatThreads) reduce_lat(const __grid_constant_
         for (int u = 0; u < kLatPer; ++u) {
             const int k = t + u * kLatThreads;
             if (k < nel) {
-                const int si = k + k / L;                    // r (L + 1) + i
+                const int r = k / L, i = k - r * L;
                 if (PLAIN) {
-                    PT[si] = DOT ? __dmul_rn(xv[u], yv[u]) : xv[u];
+                    PT[r * R.SP + i] = DOT ? __dmul_rn(xv[u], yv[u]) : xv[u];
                 } else if (DOT) {
                     const tf::d2 q = tf::apply(tf::OP_MUL, xv[u], xlv[u], xd, yv[u], ylv[u], yd);
-                    PT[si] = q.z0;
-                    E[si] = q.z1;
+                    PT[r * R.SP + i] = q.z0;
+                    ET[r * R.SE + i].x = q.z1;
                 } else {
-                    PT[si] = xv[u];
-                    if (!xd) E[si] = xlv[u];
+                    PT[r * R.SP + i] = xv[u];
+                    if (!xd) ET[r * R.SE + i].x = xlv[u];
                 }
+            }
+        }
+        // -0.0 past the end of each leaf, up to L8
+        for (int q = t; q < nl * R.L8; q += kLatThreads) {
+            const int r = q / R.L8, i = q - r * R.L8;
+            if (base + (int64_t)r * L + i >= end || i >= L) {
+                PT[r * R.SP + i] = -0.0;
+                if (!PLAIN) ET[r * R.SE + i] = make_double2(-0.0, -0.0);
             }
         }
     }
     __syncthreads();
-    // this lane's leaf (lanes >= nl idle); leaf 0 is the longest
-    const int my_len = lane < nl ? (int)min((int64_t)L, end - (base + (int64_t)lane * L)) : 0;
+    // this lane's leaf (lanes >= nl repeat the last leaf's chain; their
+    // results are never used); leaf 0 is the longest
+    const int row = min(lane, nl - 1);
     const int len0 = (int)min((int64_t)L, end - base);
     const int n8 = (len0 + 7) & ~7;
+    const double2 *Pp = reinterpret_cast<const double2 *>(PT + row * R.SP);   // (p_i, p_i+1) pairs
     tf::d2 acc = {0.0, 0.0};
     if (PLAIN) {
         if (warp == 0) {
-            const double *Pr = PT + lane * Sd;
             for (int i = 0; i < n8; i += 8) {
-                double v[8];
+                double2 v[4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = i + u < my_len ? Pr[i + u] : -0.0;
+                for (int u = 0; u < 4; ++u) v[u] = Pp[(i >> 1) + u];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc.z0 = __dadd_rn(acc.z0, v[u]);
+                for (int u = 0; u < 4; ++u) {
+                    acc.z0 = __dadd_rn(acc.z0, v[u].x);
+                    acc.z0 = __dadd_rn(acc.z0, v[u].y);
+                }
             }
         }
     } else {
         int nch = 1;
         while (nch < kLatChunks && lat_chunk_start(nch, n8) < n8) ++nch;
         if (warp == 0) {
-            const double *Pr = PT + lane * Sd;
-            double *Cr = CK + lane * Cd;
+            double *Cr = CK + lane * R.SC;
             for (int c = 0; c < nch; ++c) {
                 const int i1 = lat_chunk_start(c + 1, n8);
                 for (int i = lat_chunk_start(c, n8); i < i1; i += 8) {
-                    double v[8];
+                    double2 v[4];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = i + u < my_len ? Pr[i + u] : -0.0;
+                    for (int u = 0; u < 4; ++u) v[u] = Pp[(i >> 1) + u];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) acc.z0 = __dadd_rn(acc.z0, v[u]);
+                    for (int u = 0; u < 4; ++u) {
+                        acc.z0 = __dadd_rn(acc.z0, v[u].x);
+                        acc.z0 = __dadd_rn(acc.z0, v[u].y);
+                    }
                     if (lane < nl) Cr[i >> 3] = acc.z0;          // s_{i+7}
                 }
                 __syncwarp();
@@ -348,12 +383,13 @@ __global__ void __launch_bounds__(kLatThreads) reduce_lat(const __grid_constant_
                 for (int task = t - 64; task < nl * nk; task += kTailThreads) {
                     const int r = task / nk, k = k0 + task - r * nk;
                     const int rl = (int)min((int64_t)L, end - (base + (int64_t)r * L));
-                    double *Pr = PT + r * Sd;
-                    double sv = k ? CK[r * Cd + k - 1] : 0.0;
+                    const double *Pr = PT + r * R.SP;
+                    double2 *Er = ET + r * R.SE;
+                    double sv = k ? CK[r * R.SC + k - 1] : 0.0;
                     for (int i = 8 * k; i < min(8 * k + 8, rl); ++i) {
                         const double p = Pr[i];
                         const double sn = __dadd_rn(sv, p);
-                        Pr[i] = tf::soft::sum_err(sv, p, sn);             // t_i replaces p_i
+                        Er[i].y = tf::soft::sum_err(sv, p, sn);            // t_i
                         sv = sn;
                     }
                 }
@@ -361,25 +397,20 @@ __global__ void __launch_bounds__(kLatThreads) reduce_lat(const __grid_constant_
                 bar_arrive(1 + kLatChunks + c, 32 + kTailThreads);
             }
         } else {   // warp 1
-            const bool has_e = DOT || !xd;
-            const double *Er = E + lane * Sd, *Tr = PT + lane * Sd;
+            const double2 *Q = ET + row * R.SE;
             for (int c = 0; c < nch; ++c) {
                 bar_wait(1 + kLatChunks + c, 32 + kTailThreads);
                 const int i1 = lat_chunk_start(c + 1, n8);
                 for (int i = lat_chunk_start(c, n8); i < i1; i += 8) {
-                    double ev[8], tv[8];
+                    double2 v[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const bool in = i + u < my_len;
-                        ev[u] = in && has_e ? Er[i + u] : -0.0;
-                        tv[u] = in ? Tr[i + u] : -0.0;
-                    }
-                    if (has_e) {
+                    for (int u = 0; u < 8; ++u) v[u] = Q[i + u];
+                    if (DOT || !xd) {
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(__dadd_rn(acc.z1, ev[u]), tv[u]);
+                        for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(__dadd_rn(acc.z1, v[u].x), v[u].y);
                     } else {
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(acc.z1, tv[u]);
+                        for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(acc.z1, v[u].y);
                     }
                 }
             }
@@ -414,7 +445,7 @@ int lat_group(int64_t L, int64_t M) {
     return B;
 }
 
-size_t lat_smem(int B, int64_t L) { return ((size_t)2 * B * (L + 1) + (size_t)B * (L / 8 + 1)) * sizeof(double); }
+size_t lat_smem(int B, int64_t L) { return LatRows(L).bytes(B); }
 
 // One CTA per job with 0 or >= 2 blocks.  Thread t first reduces the aligned
 // group of G partials [tG, (t+1)G) in place (G = 2^g, G*kThreads >= nb),

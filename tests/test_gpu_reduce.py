@@ -156,3 +156,63 @@ def test_ill_conditioned_batch_full():
     assert lo.mean() < 0.05 and hi.mean() > 0.95
     pl = T.plain_dot_batched(dev(x), dev(y), offs)
     assert_bits(pl, r0, "plain twin == z0")
+
+
+@pytest.mark.parametrize("fill", [0x00, 0xFF, "counts"])
+def test_latency_schedule_any_workspace_contents(fill):
+    """Whatever the workspace holds before a call (zeros, all ones, small
+    integers at every word), repeated latency-schedule sums and dots on the
+    same workspace give the oracle's bits, plain twin included."""
+    import torch
+    n = 65536 + 77
+    x, y = synth.dot_uniform(n, seed=90)
+    gx, gy = dev(x), dev(y)
+    nb = T.lib().twofold_workspace_bytes(T.KIND_DOT, n, 1, None)
+    ws = T.workspace(nb)
+    e0, e1 = O.reduce(x, None, y, None)
+    s0, s1 = O.reduce(x)
+    for rep in range(3):
+        if fill == "counts":
+            ws.view(torch.int64)[:nb // 8] = torch.arange(nb // 8, device="cuda", dtype=torch.int64) % 300
+        else:
+            ws.fill_(fill)
+        z0, z1, fl = T.twofold_dot(gx, gy, ws=ws)
+        assert_bits(z0, [e0], f"rep {rep} z0")
+        assert_bits(z1, [e1], f"rep {rep} z1")
+        assert_flags(fl, [O.flag(e0, e1)], f"rep {rep} flag")
+        u0, u1, _ = T.twofold_sum(gx, ws=ws)              # the same workspace, after the dot
+        assert_bits(u0, [s0], f"rep {rep} sum z0")
+        assert_bits(u1, [s1], f"rep {rep} sum z1")
+        assert_bits(T.plain_dot(gx, gy, ws=ws), [O.reduce_plain(x, y)], f"rep {rep} plain")
+
+
+def test_latency_schedule_graph_replays():
+    """A dot captured in a CUDA graph (two launches with programmatic
+    dependent launch): every replay, with new data copied into the same
+    buffers, gives the oracle's bits for that data."""
+    import torch
+    n = 65536
+    gx = torch.empty(n, dtype=torch.float64, device="cuda")
+    gy = torch.empty(n, dtype=torch.float64, device="cuda")
+    ws = T.workspace(T.lib().twofold_workspace_bytes(T.KIND_DOT, n, 1, None))
+    out = (torch.empty(1, dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.float64, device="cuda"),
+           torch.empty(1, dtype=torch.uint8, device="cuda"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        T.twofold_dot(gx, gy, out=out, ws=ws)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        T.twofold_dot(gx, gy, out=out, ws=ws)
+    for rep in range(5):
+        x, y = synth.dot_uniform(n, seed=200 + rep)
+        gx.copy_(torch.from_numpy(x))
+        gy.copy_(torch.from_numpy(y))
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = O.reduce(x, None, y, None)
+        assert_bits(out[0], [e0], f"replay {rep} z0")
+        assert_bits(out[1], [e1], f"replay {rep} z1")
+        assert_flags(out[2], [O.flag(e0, e1)], f"replay {rep} flag")
