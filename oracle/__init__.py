@@ -108,6 +108,9 @@ def load(path: str) -> ctypes.CDLL:
     L.tfof_ew.argtypes = [p, i, p, p, i, i64, i64, p, p, p, i, f, f]
     L.tfof_ew_plain.argtypes = [p, i, p, i, i64, i64, p]
     L.tfof_reduce_sum.argtypes = [p, p, i64, i64, pf, pf]
+    L.tfof_reduce.argtypes = [p, p, p, p, i64, i64, i, pf, pf]
+    L.tfof_reduce_plain.argtypes = [p, p, i64, i64, i]
+    L.tfof_reduce_plain.restype = f
     return L
 
 
@@ -438,3 +441,19 @@ def reduce_sum32(x, xl=None, L=256):
     x = _f32(x)
     xl = None if xl is None else _f32(xl)
     return _pair32(lib().tfof_reduce_sum, _ptr(x), _ptr(xl), x.size, L)
+
+
+def reduce32(x, xl=None, y=None, yl=None, L=256):
+    """binary32 twofold sum (y None) or dot in the blocked pairwise order (R8)."""
+    x = _f32(x)
+    xl = None if xl is None else _f32(xl)
+    y = None if y is None else _f32(y)
+    yl = None if yl is None else _f32(yl)
+    return _pair32(lib().tfof_reduce, _ptr(x), _ptr(xl), _ptr(y), _ptr(yl), x.size, L, int(y is not None))
+
+
+def reduce32_plain(x, y=None, L=256):
+    """Plain binary32 twin of reduce32 (the same leaves and tree)."""
+    x = _f32(x)
+    y = None if y is None else _f32(y)
+    return lib().tfof_reduce_plain(_ptr(x), _ptr(y), x.size, L, int(y is not None))

@@ -374,18 +374,28 @@ void tfof_ew_plain(const int32_t *prog, int nprog, const float *const *in_hi, in
     }
 }
 
-/* ----------------------------------------------------- sum in the order R8
- * (binary32): leaves of L elements from (+0, +0) with ATF1 (ATF1.1 when the
- * input is dotted), then the pairwise tree with the odd node carried. */
-void tfof_reduce_sum(const float *xh, const float *xl, int64_t n, int64_t L, float *z0, float *z1) {
+/* ----------------------------------------------- sum and dot in the order R8
+ * (binary32): leaves of L elements from (+0, +0); a sum adds each element
+ * with ATF1 (ATF1.1 when the input is dotted), a dot adds each product
+ * x_i * y_i, formed as a twofold by the multiplication of the operand kinds
+ * (Two-Product for two dotted operands, MTF1.1 / MTF1 otherwise), with
+ * ATF1; then the pairwise tree of ATF1 with the odd node carried. */
+void tfof_reduce(const float *xh, const float *xl, const float *yh, const float *yl, int64_t n, int64_t L,
+                 int is_dot, float *z0, float *z1) {
     int64_t m = n ? (n + L - 1) / L : 0;
     if (m == 0) { *z0 = 0.0f; *z1 = 0.0f; return; }
     tfof_tf *nodes = (tfof_tf *)malloc(sizeof(tfof_tf) * (size_t)m);
     for (int64_t j = 0; j < m; ++j) {
         tfof_tf acc = {0.0f, 0.0f};
         int64_t e = (j + 1) * L < n ? (j + 1) * L : n;
-        for (int64_t i = j * L; i < e; ++i)
-            acc = xl ? tfof_atf1(acc.z0, acc.z1, xh[i], xl[i]) : tfof_atf11(acc.z0, acc.z1, xh[i]);
+        for (int64_t i = j * L; i < e; ++i) {
+            if (!is_dot) {
+                acc = xl ? tfof_atf1(acc.z0, acc.z1, xh[i], xl[i]) : tfof_atf11(acc.z0, acc.z1, xh[i]);
+            } else {
+                tfof_tf q = kinds(F_MUL, xh[i], xl ? xl[i] : 0.0f, xl == NULL, yh[i], yl ? yl[i] : 0.0f, yl == NULL);
+                acc = tfof_atf1(acc.z0, acc.z1, q.z0, q.z1);
+            }
+        }
         nodes[j] = acc;
     }
     while (m > 1) {
@@ -397,4 +407,34 @@ void tfof_reduce_sum(const float *xh, const float *xl, int64_t n, int64_t L, flo
     *z0 = nodes[0].z0;
     *z1 = nodes[0].z1;
     free(nodes);
+}
+
+void tfof_reduce_sum(const float *xh, const float *xl, int64_t n, int64_t L, float *z0, float *z1) {
+    tfof_reduce(xh, xl, NULL, NULL, n, L, 0, z0, z1);
+}
+
+/* Plain binary32 twin: the same leaves and tree with s = +0 and
+ * s = s + x_i (sum) or s = s + x_i * y_i (separate multiply and add). */
+float tfof_reduce_plain(const float *x, const float *y, int64_t n, int64_t L, int is_dot) {
+    int64_t m = n ? (n + L - 1) / L : 0;
+    if (m == 0) return 0.0f;
+    float *nodes = (float *)malloc(sizeof(float) * (size_t)m);
+    for (int64_t j = 0; j < m; ++j) {
+        float s = 0.0f;
+        int64_t e = (j + 1) * L < n ? (j + 1) * L : n;
+        for (int64_t i = j * L; i < e; ++i) {
+            if (is_dot) { float q = x[i] * y[i]; s = s + q; }
+            else        s = s + x[i];
+        }
+        nodes[j] = s;
+    }
+    while (m > 1) {
+        int64_t h = 0;
+        for (int64_t i = 0; i + 1 < m; i += 2) nodes[h++] = nodes[i] + nodes[i + 1];
+        if (m & 1) nodes[h++] = nodes[m - 1];
+        m = h;
+    }
+    float r = nodes[0];
+    free(nodes);
+    return r;
 }

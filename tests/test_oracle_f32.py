@@ -216,3 +216,92 @@ def test_sticky_flag_keeps_an_intermediate_panic():
     ins32 = [(np.ones(4, np.float32), np.full(4, 2.0 ** -30, np.float32)), (ones, None), (zero, None)]
     assert list(O.ew32(prog, ins32, mode=O.REL)[2]) == [0] * 4
     assert list(O.ew32(prog, ins32, mode=O.REL | O.STICKY)[2]) == [O.PANIC] * 4
+
+
+# ------------------------------------------------ binary32 sum and dot (R8)
+
+def test_dot32_single_term_is_two_product(pairs):
+    """A one-element dotted dot is the Two-Product pair: z0 + z1 = x y
+    exactly, z0 = RN(x y)."""
+    x, y = pairs
+    for a, b in zip(x[:500], y[:500]):
+        z0, z1 = O.reduce32([a], None, [b])
+        assert F(z0) + F(z1) == F(a) * F(b)
+        assert z0 == rn32(F(a) * F(b))
+
+
+def test_dot32_with_unit_multiplier_is_the_sum():
+    """y = 1: every Two-Product is (x, +0), and ATF1 with a +0 tail adds the
+    same bits as ATF1.1, so the dot equals the dotted sum bit for bit."""
+    rng = np.random.default_rng(5)
+    for n, L in [(1, 256), (255, 256), (1000, 7), (5000, 256), (777, 1000)]:
+        x = rand32(rng, n, -10, 10).astype(np.float32)
+        d = O.reduce32(x, None, np.ones(n, np.float32), L=L)
+        s = O.reduce_sum32(x, None, L=L)
+        assert np.array_equal(np.float32(d).view(np.uint32), np.float32(s).view(np.uint32)), (n, L)
+
+
+def test_dot32_zero_tails_equal_dotted():
+    """Materialised +0 tails give the dotted result (MTF1.1 with x1 = 0
+    adds 0 y0 = +-0 to the Two-Product tail, which keeps it)."""
+    rng = np.random.default_rng(6)
+    n = 3000
+    x = rand32(rng, n).astype(np.float32)
+    y = rand32(rng, n).astype(np.float32)
+    z = np.zeros(n, np.float32)
+    a = O.reduce32(x, None, y, None)
+    for xl, yl in [(z, None), (None, z), (z, z)]:
+        b = O.reduce32(x, xl, y, yl)
+        assert np.array_equal(np.float32(a).view(np.uint32), np.float32(b).view(np.uint32))
+
+
+def test_dot32_exact_when_everything_is_representable():
+    """Small integers: every product and partial sum is exact in binary32,
+    so z0 is the exact dot and z1 = 0, for any leaf size."""
+    rng = np.random.default_rng(7)
+    for n, L in [(10, 3), (1000, 256), (4096, 64), (999, 1)]:
+        x = rng.integers(-60, 61, n).astype(np.float32)
+        y = rng.integers(-60, 61, n).astype(np.float32)
+        z0, z1 = O.reduce32(x, None, y, None, L=L)
+        assert z0 == float(np.dot(x.astype(np.int64), y.astype(np.int64))) and z1 == 0.0
+
+
+def test_dot32_accuracy_and_z0_is_the_plain_dot():
+    """z0 is the plain binary32 dot in the same order (each step's head is the
+    rounded plain operation), and z0 + z1 is within the twofold error bound
+    of the exact dot: |err| <= u |dot| + 2 n^2 u^2 sum |x_i y_i| (u = 2^-24),
+    which plain binary32 accumulation misses by orders of magnitude on
+    cancelling data."""
+    rng = np.random.default_rng(8)
+    u = Fraction(1, 2 ** 24)
+    for n, L in [(50, 256), (700, 64), (2000, 256)]:
+        for trial in range(5):
+            x = rand32(rng, n, -8, 8).astype(np.float32)
+            y = rand32(rng, n, -8, 8).astype(np.float32)
+            z0, z1 = O.reduce32(x, None, y, None, L=L)
+            plain = O.reduce32_plain(x, y, L=L)
+            assert np.float32(z0).view(np.uint32) == np.float32(plain).view(np.uint32)
+            exact = sum(F(float(a)) * F(float(b)) for a, b in zip(x, y))
+            mag = sum(abs(F(float(a)) * F(float(b))) for a, b in zip(x, y))
+            assert abs(F(z0) + F(z1) - exact) <= u * abs(exact) + 2 * n * n * u * u * mag
+
+
+def test_plain32_twin_is_plain_float_arithmetic():
+    """The plain twin is binary32 IEEE arithmetic in the blocked order:
+    numpy float32 operations in the same order give the same bits."""
+    rng = np.random.default_rng(9)
+    for n, L in [(1, 4), (100, 7), (1000, 256), (257, 256)]:
+        x = rand32(rng, n).astype(np.float32)
+        y = rand32(rng, n).astype(np.float32)
+        for dot in (False, True):
+            nodes = []
+            for j in range(0, n, L):
+                s = np.float32(0.0)
+                for i in range(j, min(n, j + L)):
+                    s = np.float32(s + (np.float32(x[i] * y[i]) if dot else x[i]))
+                nodes.append(s)
+            while len(nodes) > 1:
+                nodes = [np.float32(nodes[i] + nodes[i + 1]) for i in range(0, len(nodes) - 1, 2)] + \
+                        ([nodes[-1]] if len(nodes) % 2 else [])
+            got = O.reduce32_plain(x, y if dot else None, L=L)
+            assert np.float32(got).view(np.uint32) == nodes[0].view(np.uint32), (n, L, dot)

@@ -99,6 +99,16 @@ MUTANTS = {
                                 [lambda: TF.test_atf1_stf1_budget32(
                                     (TF.rand32(__import__("numpy").random.default_rng(1), 3000),
                                      TF.rand32(__import__("numpy").random.default_rng(2), 3000)))]),
+    "f32_dot_drops_product_tail": (("tfof_reduce", "acc = tfof_atf1(acc.z0, acc.z1, q.z0, q.z1);",
+                                    "acc = tfof_atf11(acc.z0, acc.z1, q.z0);"),
+                                   [lambda: TF.test_dot32_single_term_is_two_product(
+                                       (TF.rand32(__import__("numpy").random.default_rng(1), 600),
+                                        TF.rand32(__import__("numpy").random.default_rng(2), 600)))]),
+    "f32_dot_leaf_off_by_one": (("tfof_reduce", "for (int64_t i = j * L; i < e; ++i) {",
+                                 "for (int64_t i = j * L + 1; i < e; ++i) {"),
+                                [TF.test_dot32_exact_when_everything_is_representable]),
+    "f32_plain_tree_drops_carry": (("tfof_reduce_plain", "if (m & 1) nodes[h++] = nodes[m - 1];", ""),
+                                   [TF.test_plain32_twin_is_plain_float_arithmetic]),
     "gauss_dtf1_drops_d0": (("tfo_dtf1", "double d0 = y0 + y1;", "double d0 = y0 + y0;"),
                             [lambda: TP.test_gauss_logs("gauss_well3", 0.1, (11.0, 11.0, 1.0)),
                              lambda: TA.test_dtf1_budget(data())]),
