@@ -668,6 +668,36 @@ def workload_ew_f32(args, rank, world, dist_on):
     }
 
 
+def workload_dot_f32(args, rank, world, dist_on):
+    """A binary32 twofold dot of 2^28 dotted elements (the paper's float
+    basis; inputs 2 GiB, beyond L2), against its plain binary32 twin: the
+    FP32 pipe is wide here, so the bound is HBM (8 B per element)."""
+    import torch
+    import paper_1401_6235_gb300 as T
+    import synth
+    n = args.n or (1 << 28)
+    gx = torch.from_numpy(synth.uniform(rank, 0, n, -1.0, 1.0).astype(np.float32)).cuda()
+    gy = torch.from_numpy(synth.uniform(rank, 1, n, -1.0, 1.0).astype(np.float32)).cuda()
+    ws = T.workspace(T.lib().twofold_workspace_bytes(T.KIND_DOT, n, 1, None))
+    out = (torch.empty(1, dtype=torch.float32, device="cuda"), torch.empty(1, dtype=torch.float32, device="cuda"),
+           torch.empty(1, dtype=torch.uint8, device="cuda"))
+    pout = torch.empty(1, dtype=torch.float32, device="cuda")
+    with ClockSampler(args.smi_index) as cs:
+        ms = time_steps(lambda: T.twofold_dot_f32(gx, gy, out=out, ws=ws), args.steps, args.warmup, dist_on)
+    plain_ms = time_steps(lambda: T.plain_dot_f32(gx, gy, out=pout, ws=ws), args.steps, args.warmup, dist_on)
+    per = ms / args.steps
+    return {
+        "metric": "binary32 twofold dot GB/s (2^28 dotted elements, 8 B/elt)", "value": 8 * n * world / (per * 1e-3) / 1e9,
+        "unit": "GB/s", "ms_per_step": per, "plain_ms_per_step": plain_ms / args.steps,
+        "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "config": {"workload": "dot_f32 x, y uniform[-1,1] float, seed = rank, L=256", "n": n,
+                   "l2": "inputs (2 GiB) larger than L2; no flush needed", "parallelism": f"replicas x{world}"},
+        "e2e": None, "gpu_launches": 2 * args.steps, "clocks": cs.summary(),
+        "_kernel_ms": per, "_ops": 0, "_bytes": 8 * n, "_units": n, "_bound": "hbm", "_dtype": "f32",
+        "_sample": None,
+    }
+
+
 def workload_criteria(args, rank, world, dist_on):
     """The paper's speed criteria for twofolds: at most 2x the plain
     arithmetic's time on data outside the caches and 10x inside them.  The
@@ -739,7 +769,8 @@ def cpu_criteria():
 
 WORKLOADS = {"ew_chain": workload_ew, "dot": workload_dot, "cond_dots": workload_cond_dots,
              "horner": workload_horner, "batch_mix": workload_batch_mix, "serve": workload_serve,
-             "ew_chain_f32": workload_ew_f32, "criteria": workload_criteria}
+             "ew_chain_f32": workload_ew_f32, "criteria": workload_criteria,
+             "dot_f32": workload_dot_f32}
 
 
 # -------------------------------------------------------------- reference

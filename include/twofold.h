@@ -255,6 +255,24 @@ int plain_dot(const double *x, const double *y, int64_t n, double *out1, const t
 int plain_dot_batched(const double *x, const double *y, const int64_t *offs, int32_t njobs,
                       double *out, const tf_params *p, void *ws, size_t ws_bytes, void *stream);
 
+/* Twofold sum and dot over binary32 twofolds (the paper's float basis), in
+ * the same blocked pairwise order as twofold_sum / twofold_dot (leaves of
+ * p->leaf elements, ATF1 / ATF1.1 accumulation, products by the operand
+ * kinds, the pairwise tree with the odd node carried); one result, its
+ * panic flag from p (binary32 defaults: REL with tau = 2^-18).  x.lo / y.lo
+ * NULL: dotted input.  Pointers are device pointers aligned to 4 bytes.
+ * ws: at least twofold_workspace_bytes(kind, n, 1, p) bytes (8-byte
+ * aligned).  n == 0 gives (+0, +0) and flag 0.  The plain twins compute
+ * the same order in plain binary32 (s + x_i, s + x_i * y_i). */
+int twofold_sum_f32(tf_in_f32 x, int64_t n, tf_out_f32 out1, const tf_params *p, void *ws, size_t ws_bytes,
+                    void *stream);
+int twofold_dot_f32(tf_in_f32 x, tf_in_f32 y, int64_t n, tf_out_f32 out1, const tf_params *p, void *ws,
+                    size_t ws_bytes, void *stream);
+int plain_sum_f32(const float *x, int64_t n, float *out1, const tf_params *p, void *ws, size_t ws_bytes,
+                  void *stream);
+int plain_dot_f32(const float *x, const float *y, int64_t n, float *out1, const tf_params *p, void *ws,
+                  size_t ws_bytes, void *stream);
+
 /* The upper levels of the reduction order over m partial results (z0[i],
  * z1[i] device arrays): the pairwise tree with the odd node carried, then
  * the panic flag, as a sum or dot ends.  When the partials are the results

@@ -111,6 +111,10 @@ SIGNATURES = {
     "twofold_ew_f32": ([_P, _I32, _P, _I32, _I64, tf_out_f32, _PP, _P], ctypes.c_int),
     "twofold_ew_jit": ([_I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
     "plain_ew_f32": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
+    "twofold_sum_f32": ([tf_in_f32, _I64, tf_out_f32, _PP, _P, _SZ, _P], ctypes.c_int),
+    "twofold_dot_f32": ([tf_in_f32, tf_in_f32, _I64, tf_out_f32, _PP, _P, _SZ, _P], ctypes.c_int),
+    "plain_sum_f32": ([_P, _I64, _P, _PP, _P, _SZ, _P], ctypes.c_int),
+    "plain_dot_f32": ([_P, _P, _I64, _P, _PP, _P, _SZ, _P], ctypes.c_int),
     "twofold_workspace_bytes": ([_I32, _I64, _I32, _PP], _SZ),
     "twofold_sum": ([_IN, _I64, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
     "twofold_dot": ([_IN, _IN, _I64, _OUT, _PP, _P, _SZ, _P], ctypes.c_int),
@@ -306,6 +310,61 @@ def plain_ew_f32(prog, his, out=None, stream=None):
                else torch.empty(n, dtype=torch.float32, device=his[0].device))
     _check(lib().plain_ew_f32(pa.ctypes.data, pa.shape[0], ptrs, len(his), n, _dev(out, "out", True),
                               _stream(stream)), "plain_ew_f32")
+    return out
+
+
+def _red32(kind, x, y, n, out, p, ws):
+    if ws is None:
+        ws = workspace(max(256, lib().twofold_workspace_bytes(kind, n, 1, _pp(p))))
+    return ws
+
+
+def twofold_sum_f32(x, xl=None, out=None, p: tf_params | None = None, ws=None, stream=None):
+    """Twofold sum of binary32 twofolds (float32 CUDA tensors) in the blocked
+    pairwise order; returns (z0, z1, flags), 1-element tensors."""
+    n = x.numel()
+    if xl is not None and xl.numel() != n:
+        raise ValueError("x and its tails must have the same length")
+    ws = _red32(KIND_SUM, x, None, n, out, p, ws)
+    hi, lo, fl = _outputs_f32(1, x.device, out)
+    _check(lib().twofold_sum_f32(tf_in_f32(_dev(x, "x"), _dev(xl, "xl")), n,
+                                 tf_out_f32(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws), ws.numel(),
+                                 _stream(stream)), "twofold_sum_f32")
+    return hi, lo, fl
+
+
+def twofold_dot_f32(x, y, xl=None, yl=None, out=None, p: tf_params | None = None, ws=None, stream=None):
+    """Twofold dot of binary32 twofolds (float32 CUDA tensors); returns (z0, z1, flags)."""
+    n = x.numel()
+    if y.numel() != n or (xl is not None and xl.numel() != n) or (yl is not None and yl.numel() != n):
+        raise ValueError("x, y and their tails must have the same length")
+    ws = _red32(KIND_DOT, x, y, n, out, p, ws)
+    hi, lo, fl = _outputs_f32(1, x.device, out)
+    _check(lib().twofold_dot_f32(tf_in_f32(_dev(x, "x"), _dev(xl, "xl")), tf_in_f32(_dev(y, "y"), _dev(yl, "yl")),
+                                 n, tf_out_f32(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws), ws.numel(),
+                                 _stream(stream)), "twofold_dot_f32")
+    return hi, lo, fl
+
+
+def plain_sum_f32(x, out=None, p: tf_params | None = None, ws=None, stream=None):
+    torch = _torch()
+    n = x.numel()
+    ws = _red32(KIND_SUM, x, None, n, out, p, ws)
+    out = torch.empty(1, dtype=torch.float32, device=x.device) if out is None else out
+    _check(lib().plain_sum_f32(_dev(x, "x"), n, _dev(out), _pp(p), _dev(ws), ws.numel(), _stream(stream)),
+           "plain_sum_f32")
+    return out
+
+
+def plain_dot_f32(x, y, out=None, p: tf_params | None = None, ws=None, stream=None):
+    torch = _torch()
+    n = x.numel()
+    if y.numel() != n:
+        raise ValueError("x and y must have the same length")
+    ws = _red32(KIND_DOT, x, y, n, out, p, ws)
+    out = torch.empty(1, dtype=torch.float32, device=x.device) if out is None else out
+    _check(lib().plain_dot_f32(_dev(x, "x"), _dev(y, "y"), n, _dev(out), _pp(p), _dev(ws), ws.numel(),
+                               _stream(stream)), "plain_dot_f32")
     return out
 
 

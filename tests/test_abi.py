@@ -119,6 +119,21 @@ def test_combine_rejects_bad_arguments(L):
     assert L.twofold_combine(FAKE, FAKE, 40, out, None, FAKE + 4, 1 << 20, None) == T.TF_ENOSPC
 
 
+def test_reduce32_rejects_bad_arguments(L):
+    """Every case fails validation before any launch."""
+    x = T.tf_in_f32(FAKE, None)
+    out = T.tf_out_f32(FAKE, FAKE, None)
+    assert L.twofold_sum_f32(x, -1, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_sum_f32(x, 10, T.tf_out_f32(FAKE + 2, FAKE, None), None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_sum_f32(T.tf_in_f32(FAKE + 1, None), 10, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_dot_f32(x, T.tf_in_f32(None, None), 10, out, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+    bad = T.params(panic_mode=7)
+    assert L.twofold_dot_f32(x, x, 10, out, ctypes.byref(bad), FAKE, 1 << 20, None) == T.TF_EINVAL
+    assert L.twofold_dot_f32(x, x, 10 ** 6, out, None, None, 0, None) == T.TF_ENOSPC   # several blocks
+    assert L.plain_sum_f32(FAKE, 10 ** 6, FAKE, None, FAKE, 64, None) == T.TF_ENOSPC
+    assert L.plain_dot_f32(FAKE, None, 10, FAKE, None, FAKE, 1 << 20, None) == T.TF_EINVAL
+
+
 def test_workspace_bound_covers_every_split(L):
     """The workspace query is an upper bound of what the call needs for any
     job mix with that total length (host arithmetic only)."""
