@@ -15,7 +15,7 @@ import math
 import os
 
 from . import (JOB_DOT, JOB_HORNER, JOB_SUM, _check, _dev, _pp, _stream, _torch, lib, tf_batch_config,
-               tf_batch_plan, tf_in, tf_job, tf_out, tf_params, workspace)
+               tf_batch_plan, tf_in, tf_job, tf_out, tf_params)
 
 
 class Job:
@@ -80,7 +80,9 @@ class Batch:
         nb = lib().twofold_batch_workspace_bytes(self._arr, n, _pp(p), cfgp)
         if n and nb == 0:
             raise ValueError("invalid batch (job kinds, sizes or configuration)")
-        self.ws = workspace(max(nb, 256))
+        # the plan's tables live in this workspace for the batch's lifetime, so
+        # it is the batch's own (not the shared scratch of the single calls)
+        self.ws = _torch().empty(max(nb, 256), dtype=_torch().uint8, device="cuda")
         self.plan = tf_batch_plan()
         _check(lib().twofold_batch_prepare(self._arr, n, _pp(p), cfgp, _dev(self.ws), self.ws.numel(),
                                            ctypes.byref(self.plan), _stream(stream)), "twofold_batch_prepare")

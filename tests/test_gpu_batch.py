@@ -107,6 +107,24 @@ def test_relaunch_and_graph_replay():
         check(jobs, ref, "graph replay")
 
 
+def test_two_prepared_batches_stay_independent():
+    """Each prepared plan keeps its tables in its own workspace: preparing a
+    second batch (and running single-job calls) leaves the first intact."""
+    jobs_a, ref_a = make_mix(5, njobs=30, big=False)
+    jobs_b, ref_b = make_mix(6, njobs=30, big=False)
+    a = B.Batch(jobs_a, cfg=B.config(32, 4096, 256))
+    b = B.Batch(jobs_b, cfg=B.config(32, 4096, 256))
+    T.twofold_dot(jobs_b[1].x, jobs_b[1].y)                 # the shared scratch of the single calls
+    for _ in range(2):
+        for j in jobs_a + jobs_b:
+            for t in j.out:
+                t.fill_(7)
+        a.launch()
+        b.launch()
+        check(jobs_a, ref_a, "batch a")
+        check(jobs_b, ref_b, "batch b")
+
+
 def test_panic_params_and_leaf():
     """tf_params (leaf, ULP panic mode) apply to every job of the batch."""
     x, y = synth.dot_uniform(50001, seed=9)
