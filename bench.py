@@ -379,12 +379,26 @@ def workload_horner(args, rank, world, dist_on):
     pout = torch.empty(x.size, dtype=torch.float64, device="cuda")
     plain_ms = time_steps(lambda: T.plain_horner_batched(gc, coff, ks, gxx, xoff, out=pout), args.steps,
                           args.warmup, dist_on)
+    del pout
+    # the same four jobs as one persistent mixed batch (autotuned points per
+    # item and CTA size), replayed from a captured CUDA graph
+    from paper_1401_6235_gb300 import batch as Bt
+    bout = [torch.empty_like(t) for t in out]
+    jobs = [Bt.horner_job(gc[int(coff[j]):int(coff[j]) + ks[j] + 1], gxx[int(xoff[j]):int(xoff[j + 1])],
+                          out=tuple(t[int(xoff[j]):int(xoff[j + 1])] for t in bout)) for j in range(len(ks))]
+    cfg = Bt.tune(jobs)
+    graph = Bt.Batch(jobs, cfg=cfg).graph()
+    batch_ms = time_steps(graph.replay, args.steps, args.warmup, dist_on) / args.steps
+    same = all(torch.equal(u.view(torch.uint8), v.view(torch.uint8)) for u, v in zip(out, bout))
     per = ms / args.steps
     steps_total = sum(ks) * npts
     return {
         "metric": "batched twofold Horner points/s (k=5,10,20,30 x 2^24)", "value": x.size * world / (per * 1e-3),
         "unit": "points/s", "ms_per_step": per, "plain_ms_per_step": plain_ms / args.steps,
         "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "persistent_batch": {"ms_per_step": batch_ms, "points_s": x.size * world / (batch_ms * 1e-3),
+                             "config": {"points_per_item": cfg.points_per_item, "threads": cfg.threads},
+                             "same_bits_as_batched_call": bool(same), "how": "twofold_batch, autotuned, graph replay"},
         "config": {"workload": "Horner (x-1)^k expanded, k in {5,10,20,30}, 2^24 points each, x~U[0.9,1.1]",
                    "n": int(x.size), "l2": "inputs 512 MiB larger than L2", "parallelism": f"replicas x{world}"},
         "gpu_launches": args.steps, "clocks": cs.summary(),
