@@ -44,7 +44,6 @@ size_t up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 class Arena {
   public:
     void init(size_t size) {
-        size_ = size;
         free_.clear();
         if (size) free_[0] = size;
         used_ = peak_ = 0;
@@ -81,12 +80,10 @@ class Arena {
             }
         }
     }
-    size_t size() const { return size_; }
-    size_t used() const { return used_; }
     size_t peak() const { return peak_; }
 
   private:
-    size_t size_ = 0, used_ = 0, peak_ = 0;
+    size_t used_ = 0, peak_ = 0;
     std::map<size_t, size_t> free_;
 };
 
