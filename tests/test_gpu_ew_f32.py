@@ -154,3 +154,37 @@ def test_host_buffer_form_f32():
     assert_bits32(hz[0].numpy(), r0, "host z0")
     assert_bits32(hz[1].numpy(), r1, "host z1")
     assert np.array_equal(hz[2].numpy(), rf)
+
+
+def test_chain_f32_full_size_sampled():
+    """The binary32 chain workload at full size (n = 2^28, the benchmark's
+    launch configuration: the specialised kernel), checked on 2^20 sampled
+    elements against the binary32 oracle."""
+    import torch
+    n = 1 << 28
+    g = {k: (torch.empty(n, dtype=torch.float32, device="cuda"), torch.empty(n, dtype=torch.float32, device="cuda"))
+         for k in "abcd"}
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([[0, 1, n - 2, n - 1], rng.choice(n, 1 << 20, replace=False)]))
+    sub = {k: (np.empty(idx.size, np.float32), np.empty(idx.size, np.float32)) for k in "abcd"}
+    chunk = 1 << 24
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        d = synth.ew_chain(e - s, seed=3000 + s // chunk)
+        sel = (idx >= s) & (idx < e)
+        for k in "abcd":
+            h = d[k + "0"].astype(np.float32)
+            lo = (d[k + "0"] - h.astype(np.float64)).astype(np.float32)
+            g[k][0][s:e].copy_(torch.from_numpy(h))
+            g[k][1][s:e].copy_(torch.from_numpy(lo))
+            sub[k][0][sel] = h[idx[sel] - s]
+            sub[k][1][sel] = lo[idx[sel] - s]
+    z0, z1, fl = T.twofold_ew_f32(T.CHAIN_SQRT_MAD_DIV, [g[k] for k in "abcd"])
+    torch.cuda.synchronize()
+    r0, r1, rf = O.ew32(T.CHAIN_SQRT_MAD_DIV, [sub[k] for k in "abcd"])
+    ti = torch.from_numpy(idx).to("cuda")
+    assert_bits32(z0[ti], r0, "z0")
+    assert_bits32(z1[ti], r1, "z1")
+    assert_flags(fl[ti], rf, "flags")
+    del g, z0, z1, fl
+    torch.cuda.empty_cache()

@@ -120,3 +120,20 @@ def test_dot32_large_both_tails_exact_workspace():
     assert_bits32(z0, np.float32([r0]), "z0")
     assert_bits32(z1, np.float32([r1]), "z1")
     assert_flags(fl, [O.flag32(r0, r1)], "flag")
+
+
+def test_dot32_full_size_bench_configuration():
+    """The binary32 dot workload at full size: 2^28 dotted elements, uniform
+    [-1, 1] floats of seed 0, the benchmark's call; the whole result against
+    the oracle."""
+    import torch
+    n = 1 << 28
+    x = synth.uniform(0, 0, n, -1.0, 1.0).astype(np.float32)
+    y = synth.uniform(0, 1, n, -1.0, 1.0).astype(np.float32)
+    z0, z1, fl = T.twofold_dot_f32(dev(x), dev(y))
+    r0, r1 = O.reduce32(x, None, y, None)
+    assert_bits32(z0, np.float32([r0]), "z0")
+    assert_bits32(z1, np.float32([r1]), "z1")
+    assert_flags(fl, [O.flag32(r0, r1)], "flag")
+    assert_bits32(T.plain_dot_f32(dev(x), dev(y)), np.float32([O.reduce32_plain(x, y)]), "plain")
+    torch.cuda.empty_cache()
