@@ -310,10 +310,21 @@ def workload_dot(args, rank, world, dist_on):
         "e2e": {"value": e2e_ms / args.steps * 1e3, "unit": "us", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 16},
         "graph": graph,
+        "latency_floor": dot_latency_floor(cs.summary().get("sm_mhz"), per * 1e3),
         "gpu_launches": 2 * args.steps, "clocks": cs.summary(),    # leaves kernel + final tree
         "_kernel_ms": per, "_ops": DOT_OPS * n, "_bytes": DOT_BYTES * n, "_units": n,
         "_sample": lambda: cpu_sample_dot(n),
     }
+
+
+def dot_latency_floor(sm_mhz, us):
+    """The order's own floor for one leaf: the z1 accumulator of a 256-element
+    leaf takes two dependent binary64 adds per element, 64 cycles each on this
+    GPU (measured), whatever else runs in parallel."""
+    mhz = sm_mhz or 2070.0
+    floor = 2 * 256 * 64 / mhz
+    return {"floor_us": floor, "frac": floor / us, "what": "512 dependent FP64 adds x 64 cycles at the sampled "
+            "SM clock (the z1 chain of one 256-element leaf); launch, terms and tree levels come on top"}
 
 
 def cpu_sample_dot(n):
