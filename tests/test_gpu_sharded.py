@@ -94,3 +94,36 @@ def test_combine_is_the_oracle_tree(m):
     assert_bits(one(c1), np.array([r[1]]), f"m={m} z1")
     assert_flags(one(cf), O.flags(np.array([r[0]]), np.array([r[1]]), mode=O.ULP, m=2.0), f"m={m} flag")
     assert np.array_equal(host(g0).view(np.uint64), z0.view(np.uint64)), "inputs left unchanged"
+
+
+def test_sharded_entry_points_single_rank_nccl():
+    """twofold_dot_sharded / twofold_sum_sharded through a real NCCL process
+    group of one rank (the all-gather and the combine on the GPU): the
+    one-call bits."""
+    import datetime
+    import os
+    import socket
+    import torch
+    import torch.distributed as dist
+    from paper_1401_6235_gb300.dist import twofold_dot_sharded, twofold_sum_sharded
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("nccl", rank=0, world_size=1, timeout=datetime.timedelta(seconds=60),
+                            device_id=torch.device("cuda", torch.cuda.current_device()))
+    try:
+        n = 1000003
+        x, y = synth.dot_uniform(n, seed=5)
+        gx, gy = dev(x), dev(y)
+        z0, z1, fl = twofold_dot_sharded(gx, gy, n, 0, 1)
+        w0, w1, wf = T.twofold_dot(gx, gy)
+        for a, b in ((z0, w0), (z1, w1), (fl, wf)):
+            assert np.array_equal(host(a).view(np.uint8), host(b).view(np.uint8))
+        s0, s1, _ = twofold_sum_sharded(gx, n, 0, 1)
+        r = O.reduce(x, L=256)
+        assert_bits(one(s0), np.array([r[0]]), "sum z0")
+        assert_bits(one(s1), np.array([r[1]]), "sum z1")
+    finally:
+        dist.destroy_process_group()
