@@ -21,9 +21,11 @@
  *  - Pinned host memory that the device maps at the same address (memory
  *    from cudaHostAlloc / cudaMallocHost under unified addressing;
  *    twofold_host_mapped tells) may stand in for device memory in the data
- *    arrays of twofold_ew and plain_ew: the kernels then read their inputs
- *    and write their results across the host link themselves.  The
- *    arithmetic is the same device code with the same bits.
+ *    arrays of twofold_ew, plain_ew, twofold_ew_f32, plain_ew_f32 and of
+ *    the single twofold_sum / twofold_dot (inputs and results; the
+ *    workspace stays device memory): the kernels then read their inputs and
+ *    write their results across the host link themselves.  The arithmetic
+ *    is the same device code with the same bits.
  *  - Device data pointers must be 8-byte aligned (flags: any alignment).
  *    Lengths are element counts; n == 0 is valid, and then data pointers
  *    that would not be read or written may be NULL.

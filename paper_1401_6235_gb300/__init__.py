@@ -385,26 +385,30 @@ def _red_out(njobs, device, out):
 
 def twofold_sum(x, xl=None, out=None, p: tf_params | None = None, ws=None, stream=None):
     """Twofold sum in the blocked pairwise order; returns (z0, z1, flags),
-    each a 1-element CUDA tensor."""
+    1-element tensors.  Inputs and outputs may be CUDA tensors or pinned host
+    tensors the device maps (the kernels then cross the host link)."""
     n = x.numel()
     nb = lib().twofold_workspace_bytes(KIND_SUM, n, 1, _pp(p))
     ws = workspace(nb) if ws is None else ws
     hi, lo, fl = _red_out(1, x.device, out)
-    _check(lib().twofold_sum(tf_in(_dev(x), _dev(xl)), n, tf_out(_dev(hi), _dev(lo), _dev(fl)),
+    _check(lib().twofold_sum(tf_in(_dev(x, "x", True), _dev(xl, "xl", True)), n,
+                             tf_out(_dev(hi, "out", True), _dev(lo, "out", True), _dev(fl, "flags", True)),
                              _pp(p), _dev(ws), ws.numel(), _stream(stream)), "twofold_sum")
     return hi, lo, fl
 
 
 def twofold_dot(x, y, xl=None, yl=None, out=None, p: tf_params | None = None, ws=None, stream=None):
+    """Twofold dot (as twofold_sum: CUDA or device-mapped pinned host tensors)."""
     n = x.numel()
     if y.numel() != n:
         raise ValueError("x and y must have the same length")
     nb = lib().twofold_workspace_bytes(KIND_DOT, n, 1, _pp(p))
     ws = workspace(nb) if ws is None else ws
     hi, lo, fl = _red_out(1, x.device, out)
-    _check(lib().twofold_dot(tf_in(_dev(x), _dev(xl)), tf_in(_dev(y), _dev(yl)), n,
-                             tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _dev(ws), ws.numel(),
-                             _stream(stream)), "twofold_dot")
+    _check(lib().twofold_dot(tf_in(_dev(x, "x", True), _dev(xl, "xl", True)),
+                             tf_in(_dev(y, "y", True), _dev(yl, "yl", True)), n,
+                             tf_out(_dev(hi, "out", True), _dev(lo, "out", True), _dev(fl, "flags", True)),
+                             _pp(p), _dev(ws), ws.numel(), _stream(stream)), "twofold_dot")
     return hi, lo, fl
 
 

@@ -216,3 +216,23 @@ def test_latency_schedule_graph_replays():
         assert_bits(out[0], [e0], f"replay {rep} z0")
         assert_bits(out[1], [e1], f"replay {rep} z1")
         assert_flags(out[2], [O.flag(e0, e1)], f"replay {rep} flag")
+
+
+@pytest.mark.parametrize("n", [1, 65536, 1000003])
+def test_dot_and_sum_on_mapped_host_buffers(n):
+    """Pinned host inputs and outputs that the device maps: the same bits as
+    device buffers (both schedules)."""
+    import torch
+    x, y = synth.dot_uniform(n, seed=n + 41)
+    hx, hy = torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()
+    z0, z1, fl = T.twofold_dot(hx, hy)
+    torch.cuda.synchronize()
+    assert not z0.is_cuda
+    d0, d1, df = T.twofold_dot(dev(x), dev(y))
+    for a, b in ((z0, d0), (z1, d1), (fl, df)):
+        assert np.array_equal(a.numpy().view(np.uint8), host(b).view(np.uint8))
+    s0, s1, sf = T.twofold_sum(hx)
+    torch.cuda.synchronize()
+    e0, e1 = O.reduce(x, L=256)
+    assert_bits(s0.numpy(), [e0], "sum z0")
+    assert_bits(s1.numpy(), [e1], "sum z1")
