@@ -364,9 +364,26 @@ def workload_cond_dots(args, rank, world, dist_on):
     pout = torch.empty(nj, dtype=torch.float64, device="cuda")
     plain_ms = time_steps(lambda: T.plain_dot_batched(gx, gy, offs, out=pout, ws=ws), args.steps, args.warmup,
                           dist_on)
+    del pout
+    # end to end: the inputs copied in from pinned host memory, the results read back, every step
+    hx, hy = torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()
+    hres = tuple(torch.empty(nj, dtype=t.dtype).pin_memory() for t in out)
+
+    def e2e_step():
+        gx.copy_(hx, non_blocking=True)
+        gy.copy_(hy, non_blocking=True)
+        T.twofold_dot_batched(gx, gy, offs, out=out, ws=ws)
+        for h, d in zip(hres, out):
+            h.copy_(d, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 4)
+    e2e_ms = time_steps(e2e_step, e2e_steps, 3, dist_on) / e2e_steps
     per = ms / args.steps
     return {
         "metric": f"batched twofold dots jobs/s ({nj} x 2^16)", "value": nj * world / (per * 1e-3),
+        "e2e": {"value": nj * world / (e2e_ms * 1e-3), "unit": "jobs/s", "ms_per_step": e2e_ms,
+                "how": "inputs copied from pinned host memory, results read back, each step",
+                "h2d_bytes_per_step": 16 * nj * n, "d2h_bytes_per_step": 17 * nj},
         "unit": "jobs/s", "ms_per_step": per, "plain_ms_per_step": plain_ms / args.steps,
         "slowdown_vs_plain": per / (plain_ms / args.steps), "gbs": DOT_BYTES * nj * n / (per * 1e-3) / 1e9,
         "config": {"workload": f"{nj} ill-conditioned dots x 2^16, cond 10^U(2,30)", "n": nj * n,
@@ -408,12 +425,24 @@ def workload_horner(args, rank, world, dist_on):
     graph = Bt.Batch(jobs, cfg=cfg).graph()
     batch_ms = time_steps(graph.replay, args.steps, args.warmup, dist_on) / args.steps
     same = all(torch.equal(u.view(torch.uint8), v.view(torch.uint8)) for u, v in zip(out, bout))
+    del bout, jobs, graph
+    # end to end: points in pinned host memory and the results written to pinned
+    # host memory by the kernel itself (device-mapped), every step
+    hx = torch.from_numpy(x).pin_memory()
+    hout = (torch.empty(x.size, dtype=torch.float64).pin_memory(), torch.empty(x.size, dtype=torch.float64).pin_memory(),
+            torch.empty(x.size, dtype=torch.uint8).pin_memory())
+    e2e_steps = max(3, args.steps // 4)
+    e2e_ms = time_steps(lambda: T.twofold_horner_batched(gc, coff, ks, hx, xoff, out=hout), e2e_steps, 3,
+                        dist_on) / e2e_steps
     per = ms / args.steps
     steps_total = sum(ks) * npts
     return {
         "metric": "batched twofold Horner points/s (k=5,10,20,30 x 2^24)", "value": x.size * world / (per * 1e-3),
         "unit": "points/s", "ms_per_step": per, "plain_ms_per_step": plain_ms / args.steps,
         "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "e2e": {"value": x.size * world / (e2e_ms * 1e-3), "unit": "points/s", "ms_per_step": e2e_ms,
+                "how": "pinned host points and results, device-mapped", "h2d_bytes_per_step": 8 * x.size,
+                "d2h_bytes_per_step": 17 * x.size},
         "persistent_batch": {"ms_per_step": batch_ms, "points_s": x.size * world / (batch_ms * 1e-3),
                              "config": {"points_per_item": cfg.points_per_item, "threads": cfg.threads},
                              "same_bits_as_batched_call": bool(same), "how": "twofold_batch, autotuned, graph replay"},

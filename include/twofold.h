@@ -21,9 +21,9 @@
  *  - Pinned host memory that the device maps at the same address (memory
  *    from cudaHostAlloc / cudaMallocHost under unified addressing;
  *    twofold_host_mapped tells) may stand in for device memory in the data
- *    arrays of twofold_ew, plain_ew, twofold_ew_f32, plain_ew_f32 and of
- *    the single twofold_sum / twofold_dot (inputs and results; the
- *    workspace stays device memory): the kernels then read their inputs and
+ *    arrays of twofold_ew, plain_ew, twofold_ew_f32, plain_ew_f32, of the
+ *    single twofold_sum / twofold_dot and of twofold_horner(_batched)
+ *    (points and results; coefficients and workspaces stay device memory): the kernels then read their inputs and
  *    write their results across the host link themselves.  The arithmetic
  *    is the same device code with the same bits.
  *  - Device data pointers must be 8-byte aligned (flags: any alignment).

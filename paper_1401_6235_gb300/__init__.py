@@ -499,12 +499,13 @@ def plain_dot_batched(x, y, offs, out=None, p: tf_params | None = None, ws=None,
 
 def twofold_horner(coef, x, out=None, p: tf_params | None = None, stream=None):
     """Twofold Horner of ascending dotted coefficients ``coef`` (CUDA float64,
-    k+1 values) at points ``x``; returns (z0, z1, flags)."""
+    k+1 values) at points ``x`` (CUDA or device-mapped pinned host tensor);
+    returns (z0, z1, flags)."""
     n = x.numel()
     hi, lo, fl = _outputs(n, x.device, out)
-    _check(lib().twofold_horner(_dev(coef), coef.numel() - 1, _dev(x), n,
-                                tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p), _stream(stream)),
-           "twofold_horner")
+    _check(lib().twofold_horner(_dev(coef), coef.numel() - 1, _dev(x, "x", True), n,
+                                tf_out(_dev(hi, "out", True), _dev(lo, "out", True), _dev(fl, "flags", True)),
+                                _pp(p), _stream(stream)), "twofold_horner")
     return hi, lo, fl
 
 
@@ -516,8 +517,9 @@ def twofold_horner_batched(coefs, coef_offs, ks, x, x_offs, out=None, p: tf_para
     nj = kk.size
     ws = workspace(lib().twofold_horner_workspace_bytes(nj)) if ws is None else ws
     hi, lo, fl = _outputs(x.numel(), x.device, out)
-    _check(lib().twofold_horner_batched(_dev(coefs), co.ctypes.data, kk.ctypes.data, nj, _dev(x),
-                                        xo.ctypes.data, tf_out(_dev(hi), _dev(lo), _dev(fl)), _pp(p),
+    _check(lib().twofold_horner_batched(_dev(coefs), co.ctypes.data, kk.ctypes.data, nj, _dev(x, "x", True),
+                                        xo.ctypes.data, tf_out(_dev(hi, "out", True), _dev(lo, "out", True),
+                                                               _dev(fl, "flags", True)), _pp(p),
                                         _dev(ws), ws.numel(), _stream(stream)), "twofold_horner_batched")
     return hi, lo, fl
 

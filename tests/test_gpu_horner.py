@@ -76,3 +76,24 @@ def test_horner_batched_many_uneven_jobs():
     assert_bits(z0, r0, "z0")
     assert_bits(z1, r1, "z1")
     assert_flags(fl, rf, "flags")
+
+
+def test_horner_on_mapped_host_buffers():
+    """Pinned host points and results that the device maps: the bits of the
+    device-buffer call (single and batched)."""
+    import torch
+    a = synth.binomial_coefs(12)
+    x = synth.horner_points(30011, seed=8)
+    hx = torch.from_numpy(x).pin_memory()
+    ga = torch.from_numpy(a).cuda()
+    z = T.twofold_horner(ga, hx)
+    torch.cuda.synchronize()
+    d = T.twofold_horner(ga, torch.from_numpy(x).cuda())
+    for u, v in zip(z, d):
+        assert not u.is_cuda
+        assert np.array_equal(u.numpy().view(np.uint8), v.cpu().numpy().view(np.uint8))
+    zb = T.twofold_horner_batched(ga, [0, 0], [12, 5], hx, [0, 10000, 30011])
+    torch.cuda.synchronize()
+    r0, r1, rf = O.horner(a, x[:10000])
+    assert np.array_equal(zb[0].numpy()[:10000].view(np.uint64), np.asarray(r0).view(np.uint64))
+    assert np.array_equal(zb[1].numpy()[:10000].view(np.uint64), np.asarray(r1).view(np.uint64))
