@@ -717,9 +717,20 @@ def workload_ew_f32(args, rank, world, dist_on):
         ms = time_steps(lambda: T.twofold_ew_f32(prog, ins, out=out), args.steps, args.warmup, dist_on)
     plain_ms = time_steps(lambda: T.plain_ew_f32(prog, [h for h, _ in ins], out=pout), args.steps, args.warmup,
                           dist_on)
+    del pout
+    # end to end: the same call on pinned host inputs and outputs that the
+    # device maps (the kernel moves every byte across the host link)
+    hins = [(t[0].cpu().pin_memory(), t[1].cpu().pin_memory()) for t in ins]
+    hout = (torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory(),
+            torch.empty(n, dtype=torch.uint8).pin_memory())
+    e2e_steps = max(3, args.steps // 8)
+    e2e_ms = time_steps(lambda: T.twofold_ew_f32(prog, hins, out=hout), e2e_steps, 3, dist_on) / e2e_steps
     per = ms / args.steps
     nbytes = EW32_BYTES * n
     return {
+        "e2e": {"value": nbytes * world / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
+                "how": "pinned host inputs and outputs, device-mapped", "h2d_bytes_per_step": 32 * n,
+                "d2h_bytes_per_step": 9 * n},
         "metric": "twofold GB/s, binary32 basis (elementwise chain sqrt((a*b+c)/d), 41 B/elt)",
         "value": nbytes * world / (per * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": per,
         "plain_ms_per_step": plain_ms / args.steps, "slowdown_vs_plain": per / (plain_ms / args.steps),
@@ -750,6 +761,19 @@ def workload_dot_f32(args, rank, world, dist_on):
     with ClockSampler(args.smi_index) as cs:
         ms = time_steps(lambda: T.twofold_dot_f32(gx, gy, out=out, ws=ws), args.steps, args.warmup, dist_on)
     plain_ms = time_steps(lambda: T.plain_dot_f32(gx, gy, out=pout, ws=ws), args.steps, args.warmup, dist_on)
+    # end to end: the inputs copied in from pinned host memory and the result read back, every step
+    hx, hy = gx.cpu().pin_memory(), gy.cpu().pin_memory()
+    hres = tuple(torch.empty(1, dtype=t.dtype).pin_memory() for t in out)
+
+    def e2e_step():
+        gx.copy_(hx, non_blocking=True)
+        gy.copy_(hy, non_blocking=True)
+        T.twofold_dot_f32(gx, gy, out=out, ws=ws)
+        for h, d in zip(hres, out):
+            h.copy_(d, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 4)
+    e2e_ms = time_steps(e2e_step, e2e_steps, 3, dist_on) / e2e_steps
     per = ms / args.steps
     return {
         "metric": "binary32 twofold dot GB/s (2^28 dotted elements, 8 B/elt)", "value": 8 * n * world / (per * 1e-3) / 1e9,
@@ -757,7 +781,10 @@ def workload_dot_f32(args, rank, world, dist_on):
         "slowdown_vs_plain": per / (plain_ms / args.steps),
         "config": {"workload": "dot_f32 x, y uniform[-1,1] float, seed = rank, L=256", "n": n,
                    "l2": "inputs (2 GiB) larger than L2; no flush needed", "parallelism": f"replicas x{world}"},
-        "e2e": None, "gpu_launches": 2 * args.steps, "clocks": cs.summary(),
+        "e2e": {"value": 8 * n * world / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
+                "how": "inputs copied from pinned host memory, result read back, each step",
+                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 9},
+        "gpu_launches": 2 * args.steps, "clocks": cs.summary(),
         "_kernel_ms": per, "_ops": 0, "_bytes": 8 * n, "_units": n, "_bound": "hbm", "_dtype": "f32",
         "_sample": None,
     }
