@@ -5,12 +5,17 @@ n = 2^28 twofolds (a, b, c: random sign x 10^U(-3,3), d: 10^U(-3,3), tails
 uniform in +-1/2 ulp), one twofold_ew launch per step.  Other workloads
 (--workload): dot (one n = 65536 dot), cond_dots (4096 ill-conditioned dots
 of 2^16 in one batched launch), horner (k in {5,10,20,30} x 2^24 points in
-one batched launch).
+one batched launch, and as a persistent batch), batch_mix (2000 uneven
+jobs in one persistent launch vs one call each), serve (the request server
+under Poisson arrivals), ew_chain_f32 / dot_f32 (the binary32 basis) and
+criteria (the paper's cached / uncached slowdown criteria).
 
 Prints ONE JSON line on rank 0.  `value` is whole-job throughput with
-inputs resident in HBM; `e2e` is the same metric through the public API with
-inputs copied from pinned host memory and results read back every step.
-`--impl reference` times the CPU oracle on a bounded sample instead.
+inputs resident in HBM; `e2e` is the same metric through the public API
+with HOST buffers every step: either copied in and out around the call, or
+pinned host buffers the device maps, which the kernel reads and writes
+across the host link itself (`e2e.how` says which).  `--impl reference`
+times the CPU oracle on a bounded sample instead.
 """
 from __future__ import annotations
 
@@ -898,6 +903,51 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+# ------------------------------------------------------------------- line
+
+def build_line(res, args, world, sms, hbm, src):
+    """The JSON line of a workload's result dict: the contract's keys, the
+    roofline of the dominant kernel (alu: the algorithms' basic FP64 ops
+    against the FP64 issue rate at the sampled clock; hbm: algorithmic bytes
+    against the measured copy bandwidth) and the CPU baseline sample."""
+    res = dict(res)
+    sample = res.pop("_sample")
+    kms, ops, nbytes = res.pop("_kernel_ms"), res.pop("_ops"), res.pop("_bytes")
+    units = res.pop("_units", None)
+    tr = TRAFFIC_PER_UNIT.get(args.workload)
+    traffic = round(tr[0] * units) if tr and units else None
+    clk = res["clocks"]["sm_mhz"] or 2070.0
+    peak_fp64 = FP64_OPS_PER_CLK_SM * sms * clk * 1e6 / 1e12
+    achieved = ops / (kms * 1e-3) / 1e12
+    bound = res.pop("_bound", "alu")
+    if ops == 0:                                   # a serving line: no single kernel to place
+        achieved = None
+    if bound == "hbm":
+        gbs = nbytes / (kms * 1e-3) / 1e9
+        res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                           "traffic": traffic, "traffic_source": tr[1] if traffic else None,
+                           "what": f"algorithmic bytes per launch / launch time vs the {src} copy bandwidth"}
+        achieved = None
+    elif achieved is None:
+        res["roofline"] = None
+    if achieved is not None:
+        res["roofline"] = {
+            "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+            "frac": achieved / peak_fp64, "traffic": traffic, "traffic_source": tr[1] if traffic else None,
+            "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
+                    f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
+    res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
+    if sample is not None and not args.no_cpu_baseline:
+        res["cpu_baseline"] = sample()
+    line = {"metric": res.pop("metric"), "value": res.pop("value"), "unit": res.pop("unit"),
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res.pop("ms_per_step"), "higher_is_better": res.pop("higher_is_better", True),
+            "scaling": "weak", "vs_baseline": None, "dtype": res.pop("_dtype", "f64"), "data": "synthetic"}
+    line.update(res)
+    return line
+
+
 # ------------------------------------------------------------------- main
 
 def main():
@@ -933,43 +983,10 @@ def main():
     entry.build() if not os.path.exists(T.LIB_PATH) else None
 
     res = WORKLOADS[args.workload](args, rank, world, dist_on)
-    sample = res.pop("_sample")
-    kms, ops, nbytes = res.pop("_kernel_ms"), res.pop("_ops"), res.pop("_bytes")
-    units = res.pop("_units", None)
-    tr = TRAFFIC_PER_UNIT.get(args.workload)
-    traffic = round(tr[0] * units) if tr and units else None
     if rank == 0:
         hbm, src = measured_peaks()
-        clk = res["clocks"]["sm_mhz"] or 2070.0
         sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak_fp64 = FP64_OPS_PER_CLK_SM * sms * clk * 1e6 / 1e12
-        achieved = ops / (kms * 1e-3) / 1e12
-        bound = res.pop("_bound", "alu")
-        if ops == 0:                                   # a serving line: no single kernel to place
-            achieved = None
-        if bound == "hbm":
-            gbs = nbytes / (kms * 1e-3) / 1e9
-            res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                               "traffic": traffic, "traffic_source": tr[1] if traffic else None,
-                               "what": f"algorithmic bytes per launch / launch time vs the {src} copy bandwidth"}
-            achieved = None
-        elif achieved is None:
-            res["roofline"] = None
-        if achieved is not None:
-            res["roofline"] = {
-            "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp64, "traffic": traffic, "traffic_source": tr[1] if traffic else None,
-            "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
-                    f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
-        res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                      "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
-        if sample is not None and not args.no_cpu_baseline:
-            res["cpu_baseline"] = sample()
-        line = {"metric": res.pop("metric"), "value": res.pop("value"), "unit": res.pop("unit"),
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": res.pop("ms_per_step"), "higher_is_better": res.pop("higher_is_better", True),
-                "scaling": "weak", "vs_baseline": None, "dtype": res.pop("_dtype", "f64"), "data": "synthetic"}
-        line.update(res)
+        line = build_line(res, args, world, sms, hbm, src)
         print(json.dumps(line), flush=True)
     if dist_on:
         import torch.distributed as dist

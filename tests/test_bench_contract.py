@@ -1,0 +1,58 @@
+"""The benchmark's output contract on the CPU: the JSON line built from a
+workload's result carries every key the contract asks for, with the
+roofline arithmetic of both bounds; and the reference arm (the CPU oracle
+on a bounded sample) prints its line and exits 0."""
+import json
+import os
+import subprocess
+import sys
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+        "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "clocks", "roofline"}
+
+
+def fake(bound):
+    res = {"metric": "m", "value": 2.0, "unit": "GB/s", "ms_per_step": 4.0, "config": {"workload": "w"},
+           "e2e": {"value": 1.0, "unit": "GB/s", "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 8},
+           "gpu_launches": 3, "clocks": {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 9},
+           "_kernel_ms": 4.0, "_ops": 8e9, "_bytes": 4e9, "_units": 1 << 28,
+           "_sample": lambda: {"value": 1.0, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": "s"}}
+    if bound == "hbm":
+        res["_bound"] = "hbm"
+        res["_dtype"] = "f32"
+    return res
+
+
+@pytest.mark.parametrize("bound", ["alu", "hbm"])
+def test_line_has_the_contract_keys(bound):
+    args = types.SimpleNamespace(workload="ew_chain", steps=3, warmup=3, no_cpu_baseline=False)
+    line = bench.build_line(fake(bound), args, 1, 152, 6784.5, "measured")
+    assert KEYS <= set(line), KEYS - set(line)
+    assert "cpu_baseline" in line and line["cpu_baseline"]["kind"] == "oracle"
+    r = line["roofline"]
+    assert r["bound"] == bound and set(r) >= {"achieved", "peak", "unit", "frac", "traffic"}
+    if bound == "alu":
+        assert r["peak"] == pytest.approx(2.0 * 152 * 2000.0 * 1e6 / 1e12)
+        assert r["achieved"] == pytest.approx(8e9 / 4e-3 / 1e12)
+    else:
+        assert r["achieved"] == pytest.approx(4e9 / 4e-3 / 1e9) and r["peak"] == 6784.5
+        assert line["dtype"] == "f32"
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert not any(k.startswith("_") for k in line)
+    json.dumps(line)
+
+
+def test_reference_arm_prints_its_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--n", "65536"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
