@@ -163,6 +163,108 @@ __global__ void __launch_bounds__(kThreads32) red32_blocks(const __grid_constant
     }
 }
 
+// The same block reduction for leaves of a multiple of 4 elements on
+// 16-byte aligned arrays: the chunk copies move 16 bytes each (a partial
+// last vector of the job copies only its valid bytes), and each leaf row of
+// 32 elements is stored as 8 vectors of 4 with the vector index XORed by
+// the row's low three bits, so that the 16-byte row reads of any 8
+// consecutive threads (one shared-memory wavefront) hit distinct banks.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(bytes) : "memory");
+}
+
+template <bool DOT, bool PLAIN, bool XD, bool YD>
+__device__ __forceinline__ void vstep32(tf::f2 &acc, float x0, float x1, float y0, float y1) {
+    if (PLAIN) {
+        acc.z0 = __fadd_rn(acc.z0, DOT ? __fmul_rn(x0, y0) : x0);
+    } else if (!DOT) {
+        acc = XD ? tf::atf11(acc.z0, acc.z1, x0) : tf::atf1(acc.z0, acc.z1, x0, x1);
+    } else {
+        const tf::f2 q = tf::apply(tf::OP_MUL, x0, x1, XD, y0, y1, YD);
+        acc = tf::atf1(acc.z0, acc.z1, q.z0, q.z1);
+    }
+}
+
+template <bool DOT, bool PLAIN, bool XD, bool YD>
+__global__ void __launch_bounds__(kThreads32) red32_blocks_v4(const __grid_constant__ Red32Args A) {
+    extern __shared__ float4 sv4[];                   // [2][narr][B][8] vectors
+    __shared__ float s0[kThreads32], s1[kThreads32];
+    static_assert(kChunk32 == 32, "a row is 8 vectors of 4");
+    const int t = threadIdx.x;
+    const int64_t m = (A.n + A.L - 1) / A.L;
+    const int64_t leaf0 = (int64_t)blockIdx.x * A.B;
+    const int nl = (int)min((int64_t)A.B, m - leaf0);
+    const int TS = A.B * 8;                           // vectors per array in a buffer
+    const int ox = 0, oxl = TS, oy = oxl + (XD || PLAIN ? 0 : TS), oyl = oy + TS;
+    const int BS = (1 + (!PLAIN && !XD) + (DOT ? 1 + (!PLAIN && !YD) : 0)) * TS;
+    const int64_t base = leaf0 * A.L;
+    const int64_t my_len = t < nl ? min(A.L, A.n - (base + (int64_t)t * A.L)) : 0;
+    const int64_t nchunk = (A.L + kChunk32 - 1) / kChunk32;
+    // thread t copies vector j = t mod 8 of rows r0, r0 + rstep, ...
+    const int j = t & 7, r0 = t >> 3, rstep = (int)blockDim.x >> 3;
+    auto issue = [&](int64_t c) {
+        const int64_t off = c * kChunk32 + 4 * j;     // first element of the vector within each leaf
+        if (off < A.L) {
+            float4 *q = sv4 + (c & 1) * BS + r0 * 8 + (j ^ (r0 & 7));
+            int64_t g = base + (int64_t)r0 * A.L + off;
+            for (int r = r0; r < nl; r += rstep, g += (int64_t)rstep * A.L) {
+                const int64_t rem = A.n - g;          // elements of the job from g on
+                if (rem <= 0) break;                  // rows are in element order
+                const int bytes = rem >= 4 ? 16 : (int)rem * 4;
+                float4 *qr = q + (r - r0) * 8 + ((j ^ (r & 7)) - (j ^ (r0 & 7)));
+                cp_async16(qr + ox, A.xh + g, bytes);
+                if (!PLAIN && !XD) cp_async16(qr + oxl, A.xl + g, bytes);
+                if (DOT) {
+                    cp_async16(qr + oy, A.yh + g, bytes);
+                    if (!PLAIN && !YD) cp_async16(qr + oyl, A.yl + g, bytes);
+                }
+            }
+        }
+        cp_commit32();
+    };
+
+    tf::f2 acc = {0.0f, 0.0f};
+    const int sw = t & 7;
+    issue(0);
+    for (int64_t c = 0; c < nchunk; ++c) {
+        if (c + 1 < nchunk) issue(c + 1);
+        else cp_commit32();
+        cp_wait_prev32();
+        __syncthreads();
+        const float4 *row = sv4 + (c & 1) * BS + t * 8;
+        const int cnt = (int)max((int64_t)0, min((int64_t)kChunk32, my_len - c * kChunk32));
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            if (4 * v >= cnt) break;
+            const int pv = v ^ sw;
+            const float4 X = row[ox + pv];
+            const float4 XL = (!PLAIN && !XD) ? row[oxl + pv] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 Y = DOT ? row[oy + pv] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 YL = (DOT && !PLAIN && !YD) ? row[oyl + pv] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int left = cnt - 4 * v;
+            vstep32<DOT, PLAIN, XD, YD>(acc, X.x, XL.x, Y.x, YL.x);
+            if (left > 1) vstep32<DOT, PLAIN, XD, YD>(acc, X.y, XL.y, Y.y, YL.y);
+            if (left > 2) vstep32<DOT, PLAIN, XD, YD>(acc, X.z, XL.z, Y.z, YL.z);
+            if (left > 3) vstep32<DOT, PLAIN, XD, YD>(acc, X.w, XL.w, Y.w, YL.w);
+        }
+        __syncthreads();
+    }
+    if (t < nl) {
+        s0[t] = acc.z0;
+        s1[t] = acc.z1;
+    }
+    __syncthreads();
+    smem_tree32<PLAIN>(s0, s1, nl);
+    if (t == 0) {
+        if (A.nblk == 1) write32<PLAIN>(A, {s0[0], s1[0]});
+        else {
+            A.part0[blockIdx.x] = s0[0];
+            A.part1[blockIdx.x] = s1[0];
+        }
+    }
+}
+
 // One CTA: thread t first folds the aligned group of G partials [tG,
 // (t+1)G) in place (G = 2^g, G kThreads32 >= nblk), a subtree, then the CTA
 // reduces the group roots.
@@ -247,9 +349,14 @@ int run32(const float *xh, const float *xl, const float *yh, const float *yl, in
         A.part1 = reinterpret_cast<float *>(static_cast<char *>(ws) + al256(sizeof(float) * (size_t)A.nblk));
     }
     const int threads = B < 32 ? 32 : B;
-    const size_t smem = tile_bytes(B);
-    auto kern = xl ? (yl ? red32_blocks<DOT, PLAIN, false, false> : red32_blocks<DOT, PLAIN, false, true>)
-                   : (yl ? red32_blocks<DOT, PLAIN, true, false> : red32_blocks<DOT, PLAIN, true, true>);
+    // 16-byte copies when every leaf starts on a 16-byte boundary
+    auto a16 = [](const float *q) { return q == nullptr || ((uintptr_t)q % 16) == 0; };
+    const bool v4 = A.L % 4 == 0 && a16(xh) && a16(xl) && a16(yh) && a16(yl);
+    const size_t smem = v4 ? 2 * (size_t)narr * B * kChunk32 * sizeof(float) : tile_bytes(B);
+    auto kern = v4 ? (xl ? (yl ? red32_blocks_v4<DOT, PLAIN, false, false> : red32_blocks_v4<DOT, PLAIN, false, true>)
+                         : (yl ? red32_blocks_v4<DOT, PLAIN, true, false> : red32_blocks_v4<DOT, PLAIN, true, true>))
+                   : (xl ? (yl ? red32_blocks<DOT, PLAIN, false, false> : red32_blocks<DOT, PLAIN, false, true>)
+                         : (yl ? red32_blocks<DOT, PLAIN, true, false> : red32_blocks<DOT, PLAIN, true, true>));
     if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                                 cudaSuccess)
         return TF_ECUDA;

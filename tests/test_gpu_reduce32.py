@@ -137,3 +137,22 @@ def test_dot32_full_size_bench_configuration():
     assert_flags(fl, [O.flag32(r0, r1)], "flag")
     assert_bits32(T.plain_dot_f32(dev(x), dev(y)), np.float32([O.reduce32_plain(x, y)]), "plain")
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("shift", [0, 1, 2, 4])
+def test_dot32_alignment_paths(shift):
+    """Arrays starting 4, 8 or 16 bytes into an allocation (the 4-byte copy
+    path when a leaf start is not 16-byte aligned, the 16-byte path
+    otherwise) with a ragged end: the same bits either way."""
+    n = 200003
+    x, y = data32(n + shift, 91)
+    xl, yl = tails32(x, 92), tails32(y, 93)
+    g = [dev(v)[shift:] for v in (x, y, xl, yl)]
+    r0, r1 = O.reduce32(x[shift:], xl[shift:], y[shift:], yl[shift:])
+    z0, z1, _ = T.twofold_dot_f32(g[0], g[1], g[2], g[3])
+    assert_bits32(z0, np.float32([r0]), f"shift {shift} z0")
+    assert_bits32(z1, np.float32([r1]), f"shift {shift} z1")
+    d0, d1 = O.reduce32(x[shift:], None, y[shift:], None, L=100)
+    w0, w1, _ = T.twofold_dot_f32(g[0], g[1], p=T.params(leaf=100, panic_tau=2.0 ** -18))
+    assert_bits32(w0, np.float32([d0]), f"shift {shift} L=100 z0")
+    assert_bits32(w1, np.float32([d1]), f"shift {shift} L=100 z1")
