@@ -143,7 +143,8 @@ def test_batched_offset_start_and_few_jobs():
 
 def test_ill_conditioned_batch_full():
     """4096 dots of 2^16 with condition 10^U(2,30): bit-exact in full; the
-    panic rate grows with the realised condition number."""
+    panic rate grows with the realised condition number (near 0 below
+    10^3.5, near 1 above 10^16, non-decreasing over two-decade bins)."""
     x, y, offs, exact, cond, _ = synth.cond_dots(4096, 1 << 16, seed=0)
     r0, r1, rf = O.dot_batched(x, None, y, None, offs)
     z0, z1, fl = T.twofold_dot_batched(dev(x), dev(y), offs)
@@ -154,6 +155,9 @@ def test_ill_conditioned_batch_full():
     lc = np.log10(cond)
     lo, hi = f[lc < 3.5], f[lc > 16]
     assert lo.mean() < 0.05 and hi.mean() > 0.95
+    # monotone over two-decade bins of the realised condition (sampling noise allowed)
+    rates = [f[(lc >= b) & (lc < b + 2)].mean() for b in range(2, 30, 2) if ((lc >= b) & (lc < b + 2)).sum() >= 20]
+    assert all(r2 >= r1 - 0.1 for r1, r2 in zip(rates, rates[1:])), rates
     pl = T.plain_dot_batched(dev(x), dev(y), offs)
     assert_bits(pl, r0, "plain twin == z0")
 
