@@ -262,3 +262,25 @@ def test_chain_full_size_sampled():
     assert_bits(pz[ti], r0, "plain twin")
     del g, ins, z0, z1, fl, pz
     torch.cuda.empty_cache()
+
+
+def test_program_beyond_2_31_elements_sampled():
+    """A two-input program over 2^31 + 3 twofolds (the largest index past 32
+    bits), checked on sampled elements including both ends."""
+    import torch
+    n = (1 << 31) + 3
+    a = synth.uniform(21, 0, n, 1.0, 2.0)
+    b = synth.uniform(21, 1, n, 1.0, 2.0)
+    ga, gb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    prog = [(O.MUL, 2, 0, 1), (O.DIV, 3, 2, 0)]
+    z0, z1, fl = T.twofold_ew(prog, [(ga, None), (gb, None)])
+    torch.cuda.synchronize()
+    idx = np.unique(np.concatenate([[0, 1, (1 << 31) - 1, 1 << 31, n - 2, n - 1],
+                                    np.random.default_rng(3).integers(0, n, 1 << 16)]))
+    r0, r1, rf = O.ew(prog, [(a[idx], None), (b[idx], None)])
+    ti = torch.from_numpy(idx).cuda()
+    assert_bits(z0[ti], r0, "z0")
+    assert_bits(z1[ti], r1, "z1")
+    assert_flags(fl[ti], rf, "flags")
+    del ga, gb, z0, z1, fl
+    torch.cuda.empty_cache()

@@ -240,3 +240,19 @@ def test_dot_and_sum_on_mapped_host_buffers(n):
     e0, e1 = O.reduce(x, L=256)
     assert_bits(s0.numpy(), [e0], "sum z0")
     assert_bits(s1.numpy(), [e1], "sum z1")
+
+
+def test_sum_beyond_2_31_elements():
+    """A dotted sum of 2^31 + 3 elements (16 GiB): element and leaf indices
+    past 32 bits; the whole result against the oracle."""
+    import torch
+    n = (1 << 31) + 3
+    x = synth.uniform(17, 0, n, -1.0, 1.0)
+    gx = torch.from_numpy(x).cuda()
+    z0, z1, fl = T.twofold_sum(gx)
+    e0, e1 = O.reduce(x, L=256)
+    assert_bits(z0, [e0], "z0")
+    assert_bits(z1, [e1], "z1")
+    assert_flags(fl, [O.flag(e0, e1)], "flag")
+    del gx
+    torch.cuda.empty_cache()
