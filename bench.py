@@ -938,7 +938,7 @@ def build_line(res, args, world, sms, hbm, src):
                     f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
     res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                   "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
-    if sample is not None and not args.no_cpu_baseline:
+    if sample is not None and not args.no_cpu_baseline and world == 1:    # rank 0 at N = 1 only
         res["cpu_baseline"] = sample()
     line = {"metric": res.pop("metric"), "value": res.pop("value"), "unit": res.pop("unit"),
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
