@@ -172,3 +172,23 @@ def test_wait_rejects_unknown_ticket():
         t = srv.submit_sum(np.ones(10))
         srv.wait(t)
         assert T.lib().twofold_server_wait(srv._h, t.id, 0, None) == T.TF_EINVAL    # already collected
+
+
+def test_wait_timeout_keeps_the_ticket():
+    """A wait that runs out returns TF_ETIMEOUT and leaves the ticket valid:
+    a later wait collects the result (a 2^26-element chain, whose inputs
+    take milliseconds to cross the host link)."""
+    n = 1 << 26
+    d = synth.ew_chain(n, seed=12)
+    ins = [(d[c + "0"], d[c + "1"]) for c in "abcd"]
+    with Server(mem_cap=8 << 30) as srv:
+        t = srv.submit_ew(T.CHAIN_SQRT_MAD_DIV, ins)
+        first = srv.wait(t, timeout_ms=0)
+        assert first is None and t.status == T.TF_ETIMEOUT
+        z = srv.wait(t)
+        assert t.status == T.TF_OK
+    idx = np.r_[0:1000, n - 1000:n]
+    r0, r1, rf = O.ew(T.CHAIN_SQRT_MAD_DIV, [(h[idx], lo[idx]) for h, lo in ins])
+    assert_bits(z[0][idx], r0, "z0")
+    assert_bits(z[1][idx], r1, "z1")
+    assert_flags(z[2][idx], rf, "flags")
