@@ -14,10 +14,14 @@
  *    plain binary64 value with no tail, which selects the paper's ".1"
  *    algorithms (see twofold_ew for the exact rule).
  *  - Unless stated otherwise, data pointers are DEVICE pointers owned by the
- *    caller (for example torch tensors); the library never allocates, frees
- *    or synchronises (the request server below is the one exception: it owns
- *    a device arena and a scheduler thread).  Every call is asynchronous on `stream` (a
- *    cudaStream_t passed as void*; NULL is the legacy default stream).
+ *    caller (for example torch tensors); the library does not allocate,
+ *    free or synchronise data memory.  The exceptions are the request server
+ *    below, which owns a device arena and a scheduler thread;
+ *    twofold_dot_noalloc, whose partials live in a static device array; and
+ *    the run-time specialised elementwise kernels, which are compiled and
+ *    loaded once per program (code memory, see twofold_ew_jit).  Every call
+ *    is asynchronous on `stream` (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream).
  *  - Pinned host memory that the device maps at the same address (memory
  *    from cudaHostAlloc / cudaMallocHost under unified addressing;
  *    twofold_host_mapped tells) may stand in for device memory in the data
