@@ -7,8 +7,9 @@ uniform in +-1/2 ulp), one twofold_ew launch per step.  Other workloads
 of 2^16 in one batched launch), horner (k in {5,10,20,30} x 2^24 points in
 one batched launch, and as a persistent batch), batch_mix (2000 uneven
 jobs in one persistent launch vs one call each), serve (the request server
-under Poisson arrivals), ew_chain_f32 / dot_f32 (the binary32 basis) and
-criteria (the paper's cached / uncached slowdown criteria).
+under Poisson arrivals), ew_chain_f32 / dot_f32 (the binary32 basis),
+criteria (the paper's cached / uncached slowdown criteria) and dot_sharded
+(one dot split over the ranks).
 
 Prints ONE JSON line on rank 0.  `value` is whole-job throughput with
 inputs resident in HBM; `e2e` is the same metric through the public API
@@ -795,6 +796,49 @@ def workload_dot_f32(args, rank, world, dist_on):
     }
 
 
+def workload_dot_sharded(args, rank, world, dist_on):
+    """One twofold dot split across the ranks (one GPU each): 2^28 dotted
+    elements per rank on aligned 2^k-leaf shards, each rank reducing its
+    shard, the 16-byte partials all-gathered and the tree finished on every
+    rank (twofold_combine); the result is the one-GPU result bit for bit.
+    Per-rank work is fixed, so scaling is weak."""
+    import torch
+    import paper_1401_6235_gb300 as T
+    import synth
+    from paper_1401_6235_gb300.dist import reduce_sharded, shard_plan
+    per_rank = args.n or (1 << 28)
+    n_total = per_rank * world
+    a, b = shard_plan(n_total, 256, world)[rank]
+    gx = torch.from_numpy(synth.uniform_slice(7, 0, a, b, -1.0, 1.0)).cuda()
+    gy = torch.from_numpy(synth.uniform_slice(7, 1, a, b, -1.0, 1.0)).cuda()
+    ws = T.workspace(T.lib().twofold_workspace_bytes(T.KIND_DOT, b - a, 1, None))
+    local_out = tuple(torch.empty(1, dtype=dt, device="cuda") for dt in (torch.float64, torch.float64, torch.uint8))
+    cws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    cout = tuple(torch.empty(1, dtype=dt, device="cuda") for dt in (torch.float64, torch.float64, torch.uint8))
+
+    def step():
+        if dist_on:
+            return reduce_sharded(lambda: T.twofold_dot(gx, gy, out=local_out, ws=ws)[:2],
+                                  lambda u, v: T.twofold_combine(u, v, out=cout, ws=cws), n_total, 256, rank, world,
+                                  gx.device)
+        z0, z1, _ = T.twofold_dot(gx, gy, out=local_out, ws=ws)
+        return T.twofold_combine(z0, z1, out=cout, ws=cws)
+
+    with ClockSampler(args.smi_index) as cs:
+        ms = time_steps(step, args.steps, args.warmup, dist_on)
+    per = ms / args.steps
+    return {
+        "metric": "sharded twofold dot, elements/s (2^28 dotted elements per GPU)",
+        "value": n_total / (per * 1e-3), "unit": "elements/s", "ms_per_step": per,
+        "config": {"workload": "one dot over all ranks, x,y ~ U[-1,1] seed 7, aligned 2^k-leaf shards, L=256",
+                   "n_total": n_total, "l2": f"inputs ({16 * (b - a) / 2**30:g} GiB per GPU) larger than L2",
+                   "parallelism": f"sharded x{world}"},
+        "e2e": None, "gpu_launches": 3 * args.steps, "clocks": cs.summary(),   # leaves, tree, combine
+        "_kernel_ms": per, "_ops": DOT_OPS * (b - a), "_bytes": DOT_BYTES * (b - a), "_units": b - a,
+        "_sample": None,
+    }
+
+
 def workload_criteria(args, rank, world, dist_on):
     """The paper's speed criteria for twofolds: at most 2x the plain
     arithmetic's time on data outside the caches and 10x inside them.  The
@@ -867,7 +911,7 @@ def cpu_criteria():
 WORKLOADS = {"ew_chain": workload_ew, "dot": workload_dot, "cond_dots": workload_cond_dots,
              "horner": workload_horner, "batch_mix": workload_batch_mix, "serve": workload_serve,
              "ew_chain_f32": workload_ew_f32, "criteria": workload_criteria,
-             "dot_f32": workload_dot_f32}
+             "dot_f32": workload_dot_f32, "dot_sharded": workload_dot_sharded}
 
 
 # -------------------------------------------------------------- reference

@@ -84,6 +84,15 @@ def uniform(seed: int, stream: int, n: int, lo: float, hi: float, out=None) -> n
     return out
 
 
+def uniform_slice(seed: int, stream: int, a: int, b: int, lo: float, hi: float) -> np.ndarray:
+    """Elements [a, b) of the stream that uniform() draws from index 0 (the
+    generator is counter-based, so any slice is regenerable on its own)."""
+    out = np.empty(b - a, np.float64)
+    L = lib()
+    _chunked(b - a, lambda s, e: L.synth_uniform(seed, stream, a + s, e - s, lo, hi, _ptr(out) + 8 * s))
+    return out
+
+
 def loguniform(seed: int, stream: int, n: int, e_lo: float, e_hi: float, signed: bool,
                out=None) -> np.ndarray:
     out = np.empty(n, np.float64) if out is None else out

@@ -86,3 +86,11 @@ def test_gloo_ranks_reduce_sharded(world, tmp_path):
     res = [np.load(tmp_path / f"rank{r}.npy") for r in range(world)]
     for r in res[1:]:
         assert np.array_equal(r.view(np.uint64), res[0].view(np.uint64))
+
+
+def test_input_slices_regenerate_on_their_own():
+    """A rank builds only its shard: the generator's slice [a, b) equals the
+    same elements of the whole stream."""
+    full = synth.uniform(7, 1, 10007, -1.0, 1.0)
+    for a, b in [(0, 10007), (256, 4096), (9999, 10007), (5, 5)]:
+        assert np.array_equal(synth.uniform_slice(7, 1, a, b, -1.0, 1.0), full[a:b])
