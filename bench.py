@@ -2,7 +2,9 @@
 
 Default workload: the elementwise twofold chain z = sqrt((a*b + c)/d) over
 n = 2^28 twofolds (a, b, c: random sign x 10^U(-3,3), d: 10^U(-3,3), tails
-uniform in +-1/2 ulp), one twofold_ew launch per step.  Other workloads
+uniform in +-1/2 ulp), one twofold_ew launch per step, beside its plain
+binary64 twin with CUDA's division and root (slowdown_vs_plain) and with
+the library's integer-pipe ones (slowdown_vs_plain_int).  Other workloads
 (--workload): dot (one n = 65536 dot), cond_dots (4096 ill-conditioned dots
 of 2^16 in one batched launch), horner (k in {5,10,20,30} x 2^24 points in
 one batched launch, and as a persistent batch), batch_mix (2000 uneven
@@ -220,6 +222,13 @@ def workload_ew(args, rank, world, dist_on):
     with ClockSampler(args.smi_index) as cs:
         ms = time_steps(step, args.steps, args.warmup, dist_on)
     plain_ms = time_steps(pstep, args.steps, args.warmup, dist_on)
+    # the plain twin again with the integer-pipe division and root that the
+    # twofold kernel uses (the same bits): the fastest plain chain here
+    prev_mode = T.plain_divsqrt(T.PLAIN_INTEGER)
+    try:
+        plain_int_ms = time_steps(pstep, args.steps, args.warmup, dist_on)
+    finally:
+        T.plain_divsqrt(prev_mode)
 
     # end to end through the public call with HOST buffers: the inputs live in
     # pinned host memory that the device maps, and the chain kernel reads them
@@ -244,6 +253,8 @@ def workload_ew(args, rank, world, dist_on):
         "value": gbs, "unit": "GB/s", "ms_per_step": per,
         "plain_ms_per_step": plain_ms / args.steps,
         "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "plain_int_ms_per_step": plain_int_ms / args.steps,
+        "slowdown_vs_plain_int": per / (plain_int_ms / args.steps),
         "mega_ops": n * world / (per * 1e-3) / 1e6,
         "config": {"workload": "ew_chain sqrt((a*b+c)/d)", "n": n, "bytes_per_elt": EW_BYTES,
                    "inputs": "a,b,c sign*10^U(-3,3), d 10^U(-3,3), tails U(+-1/2 ulp), seed = rank",
@@ -861,8 +872,15 @@ def workload_criteria(args, rank, world, dist_on):
         reps = max(10, min(2000, (1 << 27) // n))
         tf = time_steps(lambda: T.twofold_ew(prog, g, out=out), reps, args.warmup, dist_on) / reps
         pl = time_steps(lambda: T.plain_ew(prog, [h for h, _ in g], out=pout), reps, args.warmup, dist_on) / reps
+        prev_mode = T.plain_divsqrt(T.PLAIN_INTEGER)
+        try:
+            pli = time_steps(lambda: T.plain_ew(prog, [h for h, _ in g], out=pout), reps, args.warmup,
+                             dist_on) / reps
+        finally:
+            T.plain_divsqrt(prev_mode)
         rows.append({"n": n, "where": "L2" if n <= (1 << 20) else "HBM", "twofold_us": tf * 1e3,
                      "plain_us": pl * 1e3, "slowdown": tf / pl,
+                     "plain_int_us": pli * 1e3, "slowdown_vs_plain_int": tf / pli,
                      "criterion": "2x" if n > (1 << 20) else "10x", "met": tf / pl <= (2.0 if n > (1 << 20) else 10.0)})
         del g, out, pout
     top = rows[-1]

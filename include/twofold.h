@@ -182,6 +182,21 @@ int twofold_ew_jit(int32_t mode, int64_t *built, int64_t *failed);
 int plain_ew(const int32_t *prog, int32_t nprog, const double *const *in, int32_t nin,
              int64_t n, double *out, void *stream);
 
+/* Division and square root of plain_ew (binary64 only), for measuring the
+ * twofold kernels against the fastest plain twin as well as the usual one:
+ *   TF_PLAIN_NATIVE  (0, initial): CUDA's __ddiv_rn / __dsqrt_rn, what a plain
+ *                    binary64 kernel compiles to;
+ *   TF_PLAIN_INTEGER (1): the library's integer-pipe division and root, the
+ *                    ones inside the twofold kernels (Algorithms 4 and 5's
+ *                    quotient and root), correctly rounded: the same bits.
+ * mode -1 only queries.  Returns the previous mode, or TF_EINVAL for any
+ * other mode.  The setting is process-wide and read when plain_ew is
+ * called (set it while no other thread calls plain_ew).  No paper
+ * counterpart. */
+#define TF_PLAIN_NATIVE 0
+#define TF_PLAIN_INTEGER 1
+int plain_divsqrt(int32_t mode);
+
 /* ------------------------------------------- binary32 elementwise programs
  *
  * The same programs, operations, operand kinds and flags over binary32

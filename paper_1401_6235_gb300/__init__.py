@@ -108,6 +108,7 @@ SIGNATURES = {
     "twofold_host_mapped": ([_P], ctypes.c_int),
     "twofold_ew": ([_P, _I32, _P, _I32, _I64, _OUT, _PP, _P], ctypes.c_int),
     "plain_ew": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
+    "plain_divsqrt": ([_I32], ctypes.c_int),
     "twofold_ew_f32": ([_P, _I32, _P, _I32, _I64, tf_out_f32, _PP, _P], ctypes.c_int),
     "twofold_ew_jit": ([_I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
     "plain_ew_f32": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
@@ -377,6 +378,20 @@ def jit_mode(mode: int = -1):
     if prev < 0:
         raise TwofoldError(prev, "twofold_ew_jit")
     return prev, b.value, f.value
+
+
+PLAIN_NATIVE, PLAIN_INTEGER = 0, 1
+
+
+def plain_divsqrt(mode: int = -1) -> int:
+    """Select the division and square root of plain_ew (binary64):
+    PLAIN_NATIVE (CUDA's operations, the initial mode) or PLAIN_INTEGER (the
+    library's integer-pipe ones, the same bits); -1 only queries.  Returns
+    the previous mode."""
+    prev = lib().plain_divsqrt(mode)
+    if prev < 0:
+        raise TwofoldError(prev, "plain_divsqrt")
+    return prev
 
 
 def _red_out(njobs, device, out):

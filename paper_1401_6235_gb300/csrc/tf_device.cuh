@@ -303,6 +303,15 @@ __device__ __forceinline__ double apply_plain(int op, double a, double b) {
     }
 }
 
+// The same plain operation with the division and square root on the integer
+// pipes (soft::div_rn / soft::sqrt_rn: correctly rounded, the same bits).
+__device__ __forceinline__ double apply_plain_int(int op, double a, double b) {
+    if (op > OP_SQRT) op -= 5;
+    if (op == OP_DIV) return soft::div_rn(a, b);
+    if (op == OP_SQRT) return soft::sqrt_rn(a);
+    return apply_plain(op, a, b);
+}
+
 // ---------------------------------------------------------- panic flag
 struct FlagCfg {
     int mode;      // 0 REL, 1 ULP

@@ -10,6 +10,7 @@
 // conflicts), or in registers for chain-shaped programs.  The program is
 // warp-uniform, so its dispatch never diverges.  Kernels are instantiated
 // per number type and with or without the coupled operations.
+#include <atomic>
 #include "tf_host.cuh"
 #include "tf_device_f32.cuh"
 #include "tf_jit.h"
@@ -152,7 +153,8 @@ struct PlainArgs {
     T *out;
 };
 
-template <typename T>
+// INT: binary64 division and square root on the integer pipes (plain_divsqrt).
+template <typename T, bool INT>
 __global__ void __launch_bounds__(kThreads) plain_ew_kernel(const __grid_constant__ PlainArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *regs = reinterpret_cast<T *>(smem_raw);      // [ntemp][kThreads]
@@ -163,7 +165,10 @@ __global__ void __launch_bounds__(kThreads) plain_ew_kernel(const __grid_constan
             const T x = ra < A.nin ? A.in[ra][i] : regs[(ra - A.nin) * kThreads + t];
             T y = T(0);
             if (!tf::unary(op)) y = rb < A.nin ? A.in[rb][i] : regs[(rb - A.nin) * kThreads + t];
-            regs[(A.dst[s] - A.nin) * kThreads + t] = tf::apply_plain(op, x, y);
+            T r;
+            if constexpr (INT) r = tf::apply_plain_int(op, x, y);
+            else r = tf::apply_plain(op, x, y);
+            regs[(A.dst[s] - A.nin) * kThreads + t] = r;
         }
         A.out[i] = regs[(A.last - A.nin) * kThreads + t];
     }
@@ -267,6 +272,20 @@ int run_ew(const int32_t *prog, int32_t nprog, const In *in, int32_t nin, int64_
     return tfh::launch_status();
 }
 
+std::atomic<int> g_plain_int{0};      // plain_divsqrt: 1 = integer-pipe division and root
+
+template <typename T, bool INT>
+int launch_plain_generic(const PlainArgs<T> &A, int64_t n, void *stream) {
+    const size_t smem = (size_t)A.ntemp * kThreads * sizeof(T);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(plain_ew_kernel<T, INT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return TF_ECUDA;
+    const int grid = grid_for(n, smem, (const void *)plain_ew_kernel<T, INT>);
+    plain_ew_kernel<T, INT><<<grid, kThreads, smem, tfh::as_stream(stream)>>>(A);
+    return tfh::launch_status();
+}
+
 template <typename T>
 int run_plain(const int32_t *prog, int32_t nprog, const T *const *in, int32_t nin, int64_t n, T *out,
               void *stream) {
@@ -290,18 +309,16 @@ int run_plain(const int32_t *prog, int32_t nprog, const T *const *in, int32_t ni
     jp.dotted_mask = (1u << nin) - 1;
     jp.is_f32 = sizeof(T) == 4;
     jp.plain = true;
+    const bool use_int = sizeof(T) == 8 && g_plain_int.load(std::memory_order_relaxed) == TF_PLAIN_INTEGER;
+    jp.plain_int = use_int;
     const T *nolo[TF_EW_MAX_INPUTS] = {};
     typename FlagOf<T>::type fc{};
     int jst = TF_OK;
     if (tfjit::launch(jp, A.in, nolo, out, nullptr, nullptr, fc, n, tfh::as_stream(stream), &jst)) return jst;
-    const size_t smem = (size_t)A.ntemp * kThreads * sizeof(T);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(plain_ew_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        return TF_ECUDA;
-    const int grid = grid_for(n, smem, (const void *)plain_ew_kernel<T>);
-    plain_ew_kernel<T><<<grid, kThreads, smem, tfh::as_stream(stream)>>>(A);
-    return tfh::launch_status();
+    if constexpr (sizeof(T) == 8) {
+        if (use_int) return launch_plain_generic<T, true>(A, n, stream);
+    }
+    return launch_plain_generic<T, false>(A, n, stream);
 }
 
 }  // namespace
@@ -314,6 +331,12 @@ extern "C" int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, i
 extern "C" int plain_ew(const int32_t *prog, int32_t nprog, const double *const *in, int32_t nin,
                         int64_t n, double *out, void *stream) {
     return run_plain<double>(prog, nprog, in, nin, n, out, stream);
+}
+
+extern "C" int plain_divsqrt(int32_t mode) {
+    if (mode == -1) return g_plain_int.load();
+    if (mode != TF_PLAIN_NATIVE && mode != TF_PLAIN_INTEGER) return TF_EINVAL;
+    return g_plain_int.exchange(mode);
 }
 
 extern "C" int twofold_ew_f32(const int32_t *prog, int32_t nprog, const tf_in_f32 *in, int32_t nin,

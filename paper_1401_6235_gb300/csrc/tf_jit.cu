@@ -50,8 +50,8 @@ int mode_locked() {
 std::string key_of(const Prog &p) {
     std::string k(p.is_f32 ? "f" : "d");
     char buf[64];
-    std::snprintf(buf, sizeof buf, "|%d|%d|%x|%d|%d|%d|", p.nprog, p.nin, p.dotted_mask, p.flags ? 1 : 0,
-                  p.sticky ? 1 : 0, p.plain ? 1 : 0);
+    std::snprintf(buf, sizeof buf, "|%d|%d|%x|%d|%d|%d%d|", p.nprog, p.nin, p.dotted_mask, p.flags ? 1 : 0,
+                  p.sticky ? 1 : 0, p.plain ? 1 : 0, p.plain_int ? 1 : 0);
     k += buf;
     for (int s = 0; s < p.nprog; ++s) {
         std::snprintf(buf, sizeof buf, "%d,%d,%d,%d;", p.op[s], p.dst[s], p.a[s], p.b[s]);
@@ -112,7 +112,8 @@ std::string source_of(const Prog &p) {
         for (int q = 0; q < p.nprog; ++q) {
             const int op = p.op[q], a = p.a[q], b = p.b[q], d = p.dst[q];
             if (p.plain) {                       // the plain twin: heads only
-                std::snprintf(buf, sizeof buf, "      e%dr%d_0 = tf::apply_plain(%d, e%dr%d_0, %s);\n", e, d, op, e, a,
+                std::snprintf(buf, sizeof buf, "      e%dr%d_0 = tf::apply_plain%s(%d, e%dr%d_0, %s);\n", e, d,
+                              p.plain_int ? "_int" : "", op, e, a,
                               unary(op) ? "T(0)" : ("e" + std::to_string(e) + "r" + std::to_string(b) + "_0").c_str());
                 s += buf;
                 continue;

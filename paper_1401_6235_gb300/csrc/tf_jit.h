@@ -19,6 +19,7 @@ struct Prog {
     uint32_t dotted_mask;       // bit k: input k has no tail
     bool flags, sticky, is_f32;
     bool plain;                 // the plain twin: heads only, one output
+    bool plain_int;             // plain twin: division and root on the integer pipes
 };
 
 // Launches the program's specialised kernel and returns true (status: the

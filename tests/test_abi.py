@@ -159,6 +159,23 @@ def test_host_mapped_query_without_device(L):
         assert L.twofold_host_mapped(ctypes.c_void_p(a.ctypes.data)) == 0
 
 
+def test_plain_divsqrt_mode(L):
+    """The plain twin's division / root setting: -1 queries, 0 and 1 set and
+    return the previous mode, anything else is TF_EINVAL and changes nothing."""
+    prev = L.plain_divsqrt(-1)
+    assert prev == T.PLAIN_NATIVE
+    try:
+        assert L.plain_divsqrt(T.PLAIN_INTEGER) == T.PLAIN_NATIVE
+        assert L.plain_divsqrt(-1) == T.PLAIN_INTEGER
+        assert L.plain_divsqrt(2) == T.TF_EINVAL
+        assert L.plain_divsqrt(-2) == T.TF_EINVAL
+        assert L.plain_divsqrt(-1) == T.PLAIN_INTEGER
+        with pytest.raises(T.TwofoldError):
+            T.plain_divsqrt(7)
+    finally:
+        L.plain_divsqrt(prev)
+
+
 def test_batch_rejects_bad_jobs_and_configs(L):
     """Host-side checks of the mixed batch, before any device call."""
     J = T.tf_job * 2
