@@ -224,11 +224,7 @@ def workload_ew(args, rank, world, dist_on):
     plain_ms = time_steps(pstep, args.steps, args.warmup, dist_on)
     # the plain twin again with the integer-pipe division and root that the
     # twofold kernel uses (the same bits): the fastest plain chain here
-    prev_mode = T.plain_divsqrt(T.PLAIN_INTEGER)
-    try:
-        plain_int_ms = time_steps(pstep, args.steps, args.warmup, dist_on)
-    finally:
-        T.plain_divsqrt(prev_mode)
+    plain_int = time_plain_integer(T, pstep, args, dist_on)
 
     # end to end through the public call with HOST buffers: the inputs live in
     # pinned host memory that the device maps, and the chain kernel reads them
@@ -253,8 +249,7 @@ def workload_ew(args, rank, world, dist_on):
         "value": gbs, "unit": "GB/s", "ms_per_step": per,
         "plain_ms_per_step": plain_ms / args.steps,
         "slowdown_vs_plain": per / (plain_ms / args.steps),
-        "plain_int_ms_per_step": plain_int_ms / args.steps,
-        "slowdown_vs_plain_int": per / (plain_int_ms / args.steps),
+        "plain_int_ms_per_step": plain_int, "slowdown_vs_plain_int": per / plain_int,
         "mega_ops": n * world / (per * 1e-3) / 1e6,
         "config": {"workload": "ew_chain sqrt((a*b+c)/d)", "n": n, "bytes_per_elt": EW_BYTES,
                    "inputs": "a,b,c sign*10^U(-3,3), d 10^U(-3,3), tails U(+-1/2 ulp), seed = rank",
@@ -286,6 +281,16 @@ def cpu_sample_ew(n):
     return {"value": EW_BYTES * m / dt / 1e9, "unit": "GB/s", "cores": O.THREADS, "kind": "oracle",
             "sample": f"first {m} elements of the chain workload (seed 0), {reps} passes, {dt:.2f} s wall each "
                       f"(~{reps * dt * O.THREADS:.0f} core-seconds in all)"}
+
+
+def time_plain_integer(T, call, args, dist_on):
+    """The plain twin timed again with the integer-pipe routines of
+    plain_arith (the same bits); returns ms per step."""
+    prev = T.plain_arith(T.PLAIN_INTEGER)
+    try:
+        return time_steps(call, args.steps, args.warmup, dist_on) / args.steps
+    finally:
+        T.plain_arith(prev)
 
 
 def workload_dot(args, rank, world, dist_on):
@@ -431,6 +436,8 @@ def workload_horner(args, rank, world, dist_on):
     pout = torch.empty(x.size, dtype=torch.float64, device="cuda")
     plain_ms = time_steps(lambda: T.plain_horner_batched(gc, coff, ks, gxx, xoff, out=pout), args.steps,
                           args.warmup, dist_on)
+    plain_int = time_plain_integer(T, lambda: T.plain_horner_batched(gc, coff, ks, gxx, xoff, out=pout), args,
+                                   dist_on)
     del pout
     # the same four jobs as one persistent mixed batch (autotuned points per
     # item and CTA size), replayed from a captured CUDA graph
@@ -456,7 +463,8 @@ def workload_horner(args, rank, world, dist_on):
     return {
         "metric": "batched twofold Horner points/s (k=5,10,20,30 x 2^24)", "value": x.size * world / (per * 1e-3),
         "unit": "points/s", "ms_per_step": per, "plain_ms_per_step": plain_ms / args.steps,
-        "slowdown_vs_plain": per / (plain_ms / args.steps),
+        "slowdown_vs_plain": per / (plain_ms / args.steps), "plain_int_ms_per_step": plain_int,
+        "slowdown_vs_plain_int": per / plain_int,
         "e2e": {"value": x.size * world / (e2e_ms * 1e-3), "unit": "points/s", "ms_per_step": e2e_ms,
                 "how": "pinned host points and results, device-mapped", "h2d_bytes_per_step": 8 * x.size,
                 "d2h_bytes_per_step": 17 * x.size},
@@ -872,12 +880,12 @@ def workload_criteria(args, rank, world, dist_on):
         reps = max(10, min(2000, (1 << 27) // n))
         tf = time_steps(lambda: T.twofold_ew(prog, g, out=out), reps, args.warmup, dist_on) / reps
         pl = time_steps(lambda: T.plain_ew(prog, [h for h, _ in g], out=pout), reps, args.warmup, dist_on) / reps
-        prev_mode = T.plain_divsqrt(T.PLAIN_INTEGER)
+        prev_mode = T.plain_arith(T.PLAIN_INTEGER)
         try:
             pli = time_steps(lambda: T.plain_ew(prog, [h for h, _ in g], out=pout), reps, args.warmup,
                              dist_on) / reps
         finally:
-            T.plain_divsqrt(prev_mode)
+            T.plain_arith(prev_mode)
         rows.append({"n": n, "where": "L2" if n <= (1 << 20) else "HBM", "twofold_us": tf * 1e3,
                      "plain_us": pl * 1e3, "slowdown": tf / pl,
                      "plain_int_us": pli * 1e3, "slowdown_vs_plain_int": tf / pli,

@@ -182,20 +182,24 @@ int twofold_ew_jit(int32_t mode, int64_t *built, int64_t *failed);
 int plain_ew(const int32_t *prog, int32_t nprog, const double *const *in, int32_t nin,
              int64_t n, double *out, void *stream);
 
-/* Division and square root of plain_ew (binary64 only), for measuring the
- * twofold kernels against the fastest plain twin as well as the usual one:
- *   TF_PLAIN_NATIVE  (0, initial): CUDA's __ddiv_rn / __dsqrt_rn, what a plain
- *                    binary64 kernel compiles to;
- *   TF_PLAIN_INTEGER (1): the library's integer-pipe division and root, the
- *                    ones inside the twofold kernels (Algorithms 4 and 5's
- *                    quotient and root), correctly rounded: the same bits.
+/* Arithmetic of the plain binary64 twins, for measuring the twofold kernels
+ * against the fastest plain twin as well as the usual one:
+ *   TF_PLAIN_NATIVE  (0, initial): CUDA's operations, what a plain binary64
+ *                    kernel compiles to (__ddiv_rn, __dsqrt_rn, __dmul_rn);
+ *   TF_PLAIN_INTEGER (1): the library's integer-pipe routines where they are
+ *                    faster on this GPU, the ones the twofold kernels use:
+ *                    the division and square root of plain_ew (Algorithms 4
+ *                    and 5's quotient and root) and the multiplication of
+ *                    plain_horner(_batched).  All are correctly rounded: the
+ *                    results are the same bits.
  * mode -1 only queries.  Returns the previous mode, or TF_EINVAL for any
- * other mode.  The setting is process-wide and read when plain_ew is
- * called (set it while no other thread calls plain_ew).  No paper
- * counterpart. */
+ * other mode.  The setting is process-wide and read when a plain call is
+ * made (set it while no other thread makes one).  The plain sum and dot
+ * keep the native operations in both modes (an integer multiplication made
+ * the plain dot slower), as do the binary32 twins.  No paper counterpart. */
 #define TF_PLAIN_NATIVE 0
 #define TF_PLAIN_INTEGER 1
-int plain_divsqrt(int32_t mode);
+int plain_arith(int32_t mode);
 
 /* ------------------------------------------- binary32 elementwise programs
  *

@@ -108,7 +108,7 @@ SIGNATURES = {
     "twofold_host_mapped": ([_P], ctypes.c_int),
     "twofold_ew": ([_P, _I32, _P, _I32, _I64, _OUT, _PP, _P], ctypes.c_int),
     "plain_ew": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
-    "plain_divsqrt": ([_I32], ctypes.c_int),
+    "plain_arith": ([_I32], ctypes.c_int),
     "twofold_ew_f32": ([_P, _I32, _P, _I32, _I64, tf_out_f32, _PP, _P], ctypes.c_int),
     "twofold_ew_jit": ([_I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
     "plain_ew_f32": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
@@ -383,14 +383,15 @@ def jit_mode(mode: int = -1):
 PLAIN_NATIVE, PLAIN_INTEGER = 0, 1
 
 
-def plain_divsqrt(mode: int = -1) -> int:
-    """Select the division and square root of plain_ew (binary64):
-    PLAIN_NATIVE (CUDA's operations, the initial mode) or PLAIN_INTEGER (the
-    library's integer-pipe ones, the same bits); -1 only queries.  Returns
-    the previous mode."""
-    prev = lib().plain_divsqrt(mode)
+def plain_arith(mode: int = -1) -> int:
+    """Select the arithmetic of the plain binary64 twins: PLAIN_NATIVE
+    (CUDA's operations, the initial mode) or PLAIN_INTEGER (the library's
+    integer-pipe division and root in plain_ew, multiplication in
+    plain_horner: the same bits); -1 only queries.  Returns the previous
+    mode."""
+    prev = lib().plain_arith(mode)
     if prev < 0:
-        raise TwofoldError(prev, "plain_divsqrt")
+        raise TwofoldError(prev, "plain_arith")
     return prev
 
 

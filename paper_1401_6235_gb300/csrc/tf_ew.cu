@@ -10,7 +10,6 @@
 // conflicts), or in registers for chain-shaped programs.  The program is
 // warp-uniform, so its dispatch never diverges.  Kernels are instantiated
 // per number type and with or without the coupled operations.
-#include <atomic>
 #include "tf_host.cuh"
 #include "tf_device_f32.cuh"
 #include "tf_jit.h"
@@ -153,7 +152,7 @@ struct PlainArgs {
     T *out;
 };
 
-// INT: binary64 division and square root on the integer pipes (plain_divsqrt).
+// INT: binary64 division and square root on the integer pipes (plain_arith).
 template <typename T, bool INT>
 __global__ void __launch_bounds__(kThreads) plain_ew_kernel(const __grid_constant__ PlainArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -272,8 +271,6 @@ int run_ew(const int32_t *prog, int32_t nprog, const In *in, int32_t nin, int64_
     return tfh::launch_status();
 }
 
-std::atomic<int> g_plain_int{0};      // plain_divsqrt: 1 = integer-pipe division and root
-
 template <typename T, bool INT>
 int launch_plain_generic(const PlainArgs<T> &A, int64_t n, void *stream) {
     const size_t smem = (size_t)A.ntemp * kThreads * sizeof(T);
@@ -309,7 +306,7 @@ int run_plain(const int32_t *prog, int32_t nprog, const T *const *in, int32_t ni
     jp.dotted_mask = (1u << nin) - 1;
     jp.is_f32 = sizeof(T) == 4;
     jp.plain = true;
-    const bool use_int = sizeof(T) == 8 && g_plain_int.load(std::memory_order_relaxed) == TF_PLAIN_INTEGER;
+    const bool use_int = sizeof(T) == 8 && tfh::plain_integer();
     jp.plain_int = use_int;
     const T *nolo[TF_EW_MAX_INPUTS] = {};
     typename FlagOf<T>::type fc{};
@@ -333,10 +330,10 @@ extern "C" int plain_ew(const int32_t *prog, int32_t nprog, const double *const 
     return run_plain<double>(prog, nprog, in, nin, n, out, stream);
 }
 
-extern "C" int plain_divsqrt(int32_t mode) {
-    if (mode == -1) return g_plain_int.load();
+extern "C" int plain_arith(int32_t mode) {
+    if (mode == -1) return tfh::g_plain_mode.load();
     if (mode != TF_PLAIN_NATIVE && mode != TF_PLAIN_INTEGER) return TF_EINVAL;
-    return g_plain_int.exchange(mode);
+    return tfh::g_plain_mode.exchange(mode);
 }
 
 extern "C" int twofold_ew_f32(const int32_t *prog, int32_t nprog, const tf_in_f32 *in, int32_t nin,

@@ -48,7 +48,9 @@ __device__ __forceinline__ int job_at(const HTab &T, int njobs, int64_t i) {
     return lo;
 }
 
-template <bool PLAIN>
+// IMUL (plain twin only): the multiplication s * x on the integer pipes
+// (correctly rounded, the same bits; plain_arith).
+template <bool PLAIN, bool IMUL = false>
 __global__ void __launch_bounds__(kThreads) horner_kernel(const __grid_constant__ HArgs A) {
     for (int64_t i = A.n0 + (int64_t)blockIdx.x * kThreads + threadIdx.x; i < A.n1;
          i += (int64_t)gridDim.x * kThreads) {
@@ -58,7 +60,12 @@ __global__ void __launch_bounds__(kThreads) horner_kernel(const __grid_constant_
         const double x = A.x[i];
         if (PLAIN) {
             double s = __ldg(a + k);
-            for (int c = k - 1; c >= 0; --c) s = __dadd_rn(__dmul_rn(s, x), __ldg(a + c));
+            for (int c = k - 1; c >= 0; --c) {
+                double sx;
+                if constexpr (IMUL) sx = tf::soft::mul_rn(s, x);
+                else sx = __dmul_rn(s, x);
+                s = __dadd_rn(sx, __ldg(a + c));
+            }
             A.out_plain[i] = s;
         } else {
             tf::d2 s = {__ldg(a + k), 0.0};
@@ -74,6 +81,17 @@ __global__ void __launch_bounds__(kThreads) horner_kernel(const __grid_constant_
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+template <bool PLAIN, bool IMUL>
+int launch(const HArgs &A, int64_t npts, cudaStream_t s) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, horner_kernel<PLAIN, IMUL>, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t want = (npts + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)tfh::sm_count() * per_sm;
+    horner_kernel<PLAIN, IMUL><<<(unsigned)(want < cap ? want : cap), kThreads, 0, s>>>(A);
+    return tfh::launch_status();
+}
 
 template <bool PLAIN>
 int run(const double *coefs, const int32_t *coff, const int32_t *ks, int njobs, const double *x,
@@ -116,13 +134,8 @@ int run(const double *coefs, const int32_t *coff, const int32_t *ks, int njobs, 
         A.tab.coff = reinterpret_cast<const int32_t *>(w + b0);
         A.tab.k = reinterpret_cast<const int32_t *>(w + b0 + b1);
     }
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, horner_kernel<PLAIN>, kThreads, 0);
-    if (per_sm < 1) per_sm = 1;
-    const int64_t want = (n1 - n0 + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)tfh::sm_count() * per_sm;
-    horner_kernel<PLAIN><<<(unsigned)(want < cap ? want : cap), kThreads, 0, s>>>(A);
-    return tfh::launch_status();
+    if (PLAIN && tfh::plain_integer()) return launch<PLAIN, true>(A, n1 - n0, s);
+    return launch<PLAIN, false>(A, n1 - n0, s);
 }
 
 }  // namespace

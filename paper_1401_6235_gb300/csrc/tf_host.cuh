@@ -2,6 +2,7 @@
 // defaults, argument checks, launch-error mapping.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstddef>
@@ -36,6 +37,11 @@ inline bool params_ok(const tf_params *p) {
     if (!(p->panic_tau >= 0.0) || !(p->panic_ulps >= 0.0)) return false;   // also rejects NaN
     return true;
 }
+
+// plain_arith: TF_PLAIN_INTEGER makes the plain binary64 twins use the
+// integer-pipe routines of tf_soft.cuh where they are faster (same bits).
+inline std::atomic<int> g_plain_mode{TF_PLAIN_NATIVE};
+inline bool plain_integer() { return g_plain_mode.load(std::memory_order_relaxed) == TF_PLAIN_INTEGER; }
 
 inline int leaf_of(const tf_params *p) { return p ? p->leaf : kDefaultLeaf; }
 

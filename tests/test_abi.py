@@ -159,21 +159,21 @@ def test_host_mapped_query_without_device(L):
         assert L.twofold_host_mapped(ctypes.c_void_p(a.ctypes.data)) == 0
 
 
-def test_plain_divsqrt_mode(L):
+def test_plain_arith_mode(L):
     """The plain twin's division / root setting: -1 queries, 0 and 1 set and
     return the previous mode, anything else is TF_EINVAL and changes nothing."""
-    prev = L.plain_divsqrt(-1)
+    prev = L.plain_arith(-1)
     assert prev == T.PLAIN_NATIVE
     try:
-        assert L.plain_divsqrt(T.PLAIN_INTEGER) == T.PLAIN_NATIVE
-        assert L.plain_divsqrt(-1) == T.PLAIN_INTEGER
-        assert L.plain_divsqrt(2) == T.TF_EINVAL
-        assert L.plain_divsqrt(-2) == T.TF_EINVAL
-        assert L.plain_divsqrt(-1) == T.PLAIN_INTEGER
+        assert L.plain_arith(T.PLAIN_INTEGER) == T.PLAIN_NATIVE
+        assert L.plain_arith(-1) == T.PLAIN_INTEGER
+        assert L.plain_arith(2) == T.TF_EINVAL
+        assert L.plain_arith(-2) == T.TF_EINVAL
+        assert L.plain_arith(-1) == T.PLAIN_INTEGER
         with pytest.raises(T.TwofoldError):
-            T.plain_divsqrt(7)
+            T.plain_arith(7)
     finally:
-        L.plain_divsqrt(prev)
+        L.plain_arith(prev)
 
 
 def test_batch_rejects_bad_jobs_and_configs(L):
