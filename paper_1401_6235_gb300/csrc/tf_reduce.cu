@@ -73,6 +73,12 @@ __device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_grou
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// Four consecutive doubles from a 16-byte aligned address, as two 16-byte loads.
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // One element of a leaf: acc = ATF1(acc, term) (ATF1.1 for a dotted sum).
 template <bool DOT, bool PLAIN>
 __device__ __forceinline__ void leaf_step(tf::d2 &acc, double x0, double x1, bool xd, double y0, double y1,
@@ -109,7 +115,12 @@ __device__ __forceinline__ void write_result(const RedArgs &A, int j, tf::d2 r) 
 // leaf t's row (used by the memory-bound plain twin); otherwise thread t
 // reads its leaf straight from global memory through L1 (the twofold step
 // is compute-bound and barrier-free this way).
-template <bool DOT, bool PLAIN, bool STAGED>
+// The twofold (not STAGED) kernel is specialised on the operand kinds KD
+// (bit 0: x dotted, bit 1: y dotted or no y), so its leaf step has no
+// run-time dispatch; when every array's leaf starts on a 16-byte boundary
+// (L even, aligned arrays: uniform over a CTA) it reads 16-byte pairs, four
+// elements per step, and the ragged end of the leaf one element at a time.
+template <bool DOT, bool PLAIN, bool STAGED, int KD = 3>
 __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant__ RedArgs A) {
     extern __shared__ double stage[];                // [2][narr][B][C+1] when STAGED
     __shared__ double s0[kThreads], s1[kThreads];
@@ -129,9 +140,26 @@ __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant_
     const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
     tf::d2 acc = {0.0, 0.0};
     if (!STAGED) {
-        for (int64_t i = lb; i < lb + llen; ++i)
-            leaf_step<DOT, PLAIN>(acc, A.xh[i], xd ? 0.0 : A.xl[i], xd, DOT ? A.yh[i] : 0.0,
-                                  (DOT && !yd) ? A.yl[i] : 0.0, yd);
+        constexpr bool XD = (KD & 1) != 0, YD = (KD & 2) != 0;
+        const double *X = A.xh + lb, *XL = XD ? nullptr : A.xl + lb;
+        const double *Y = DOT ? A.yh + lb : nullptr, *YL = (DOT && !YD) ? A.yl + lb : nullptr;
+        int64_t i = 0;
+        const bool vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(XL) |
+                           reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(YL)) & 15) == 0;
+        if (!PLAIN && vec) {
+            for (; i + 4 <= llen; i += 4) {
+                double x[4], xl[4] = {0.0, 0.0, 0.0, 0.0}, y[4] = {0.0, 0.0, 0.0, 0.0}, yl[4] = {0.0, 0.0, 0.0, 0.0};
+                ld4(X + i, x);
+                if (!XD) ld4(XL + i, xl);
+                if (DOT) ld4(Y + i, y);
+                if (DOT && !YD) ld4(YL + i, yl);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) leaf_step<DOT, PLAIN>(acc, x[u], xl[u], XD, y[u], yl[u], YD);
+            }
+        }
+        for (; i < llen; ++i)
+            leaf_step<DOT, PLAIN>(acc, X[i], XD ? 0.0 : XL[i], XD, DOT ? Y[i] : 0.0, (DOT && !YD) ? YL[i] : 0.0,
+                                  YD);
     } else {
         const int B = A.B, C = A.C, S = C + 1, narr = A.narr;
         const double *src[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -593,7 +621,7 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
                                                          (int)smem) != cudaSuccess)
                 return TF_ECUDA;
             if (tfh::launch_pdl(reduce_lat<DOT, PLAIN>, nblk, kLatThreads, smem, s, A) != cudaSuccess) return TF_ECUDA;
-        } else if (PLAIN) {
+        } else if constexpr (PLAIN) {
             const size_t smem = (size_t)2 * A.narr * B * (A.C + 1) * sizeof(double);
             if (smem > 48 * 1024 && cudaFuncSetAttribute(reduce_blocks<DOT, PLAIN, true>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -602,8 +630,16 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
             if (tfh::launch_pdl(reduce_blocks<DOT, PLAIN, true>, nblk, kThreads, smem, s, A) != cudaSuccess)
                 return TF_ECUDA;
         } else {
-            if (tfh::launch_pdl(reduce_blocks<DOT, PLAIN, false>, nblk, kThreads, 0, s, A) != cudaSuccess)
-                return TF_ECUDA;
+            // operand kinds: bit 0 x dotted, bit 1 y dotted (or a sum)
+            const int kd = (xl == nullptr ? 1 : 0) | (!DOT || yl == nullptr ? 2 : 0);
+            cudaError_t e;
+            switch (kd) {
+            case 0: e = tfh::launch_pdl(reduce_blocks<DOT, false, false, 0>, nblk, kThreads, 0, s, A); break;
+            case 1: e = tfh::launch_pdl(reduce_blocks<DOT, false, false, 1>, nblk, kThreads, 0, s, A); break;
+            case 2: e = tfh::launch_pdl(reduce_blocks<DOT, false, false, 2>, nblk, kThreads, 0, s, A); break;
+            default: e = tfh::launch_pdl(reduce_blocks<DOT, false, false, 3>, nblk, kThreads, 0, s, A); break;
+            }
+            if (e != cudaSuccess) return TF_ECUDA;
         }
     }
     if (need_final && tfh::launch_pdl(reduce_final<PLAIN>, njobs, kThreads, 0, s, A) != cudaSuccess)
