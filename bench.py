@@ -69,6 +69,18 @@ TRAFFIC_PER_UNIT = {
     "dot_f32": ((268.462e6 + 3.952e6) / (1 << 25), "profiles/red32_blocks_dot_f32_2e28.md"),
 }
 
+# ncu pipe activity of the dominant kernel (fraction of its peak sustained
+# rate: FP64 pipe, integer ALU pipe, instruction issue) from the committed
+# profiles: the binary64 kernels run part of their arithmetic on the integer
+# pipes, so the alu roofline's frac (algorithmic FP64 operations against the
+# FP64 pipe alone) can exceed 1 while neither pipe is full.
+PIPES = {
+    "ew_chain": ({"fp64": 0.731, "alu": 0.681, "issue": 0.600}, "profiles/tf_jit_ew_chain_n2e28.md"),
+    "horner": ({"fp64": 0.808, "alu": 0.774, "issue": 0.591}, "profiles/horner_kernel_k5-30_2e24.md"),
+    "cond_dots": ({"fp64": 0.290, "alu": 0.444, "issue": 0.330}, "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
+    "dot": ({"fp64": 0.252, "alu": 0.081}, "profiles/reduce_lat_dot_n65536.md"),
+}
+
 
 def measured_peaks():
     try:
@@ -1006,6 +1018,9 @@ def build_line(res, args, world, sms, hbm, src):
             "frac": achieved / peak_fp64, "traffic": traffic, "traffic_source": tr[1] if traffic else None,
             "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
                     f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
+        pipes = PIPES.get(args.workload)
+        if pipes:
+            res["roofline"]["ncu_pipes"] = dict(pipes[0], source=pipes[1])
     res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                   "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
     if sample is not None and not args.no_cpu_baseline and world == 1:    # rank 0 at N = 1 only

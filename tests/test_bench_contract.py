@@ -41,6 +41,9 @@ def test_line_has_the_contract_keys(bound):
     if bound == "alu":
         assert r["peak"] == pytest.approx(2.0 * 152 * 2000.0 * 1e6 / 1e12)
         assert r["achieved"] == pytest.approx(8e9 / 4e-3 / 1e12)
+        # the chain kernel's pipe activity, named with the profile it comes from
+        p = r["ncu_pipes"]
+        assert 0 < p["fp64"] <= 1 and 0 < p["alu"] <= 1 and os.path.exists(os.path.join(ROOT, p["source"]))
     else:
         assert r["achieved"] == pytest.approx(4e9 / 4e-3 / 1e9) and r["peak"] == 6784.5
         assert line["dtype"] == "f32"
