@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "tf_host.cuh"
+#include "tf_leaf.cuh"
 
 namespace {
 
@@ -83,20 +84,29 @@ __global__ void __launch_bounds__(T) batch_kernel(const __grid_constant__ BArgs 
             }
             continue;
         }
-        // reduction item: leaves [w.y B, w.y B + nl), one per thread, then the block's subtree
+        // reduction item: leaves [w.y B, w.y B + nl), one per thread, then the
+        // block's subtree; dotted sums and dots walk their leaves with the
+        // specialised tf::leaf_walk (16-byte loads), jobs with tails with the
+        // general step (fewer registers for the whole kernel)
         const bool xd = J.xl == nullptr, yd = J.yl == nullptr;
         const int64_t leaf0 = (int64_t)w.y * A.B;
         const int nl = (int)max((int64_t)0, min((int64_t)A.B, J.m - leaf0));
-        tf::d2 acc = {0.0, 0.0};
         if (t < nl) {
             const int64_t lb = (leaf0 + t) * A.L, le = min(J.n, lb + A.L);
-            for (int64_t i = lb; i < le; ++i) {
-                if (J.kind == TF_JOB_DOT) {
-                    const tf::d2 p = tf::apply(tf::OP_MUL, J.xh[i], xd ? 0.0 : J.xl[i], xd, J.yh[i],
-                                               yd ? 0.0 : J.yl[i], yd);
-                    acc = tf::atf1(acc.z0, acc.z1, p.z0, p.z1);
-                } else {
-                    acc = xd ? tf::atf11(acc.z0, acc.z1, J.xh[i]) : tf::atf1(acc.z0, acc.z1, J.xh[i], J.xl[i]);
+            tf::d2 acc = {0.0, 0.0};
+            if (J.kind == TF_JOB_DOT && xd && yd) {
+                acc = tf::leaf_walk<true, true, true>(J.xh + lb, nullptr, J.yh + lb, nullptr, le - lb);
+            } else if (J.kind != TF_JOB_DOT && xd) {
+                acc = tf::leaf_walk<false, true, true>(J.xh + lb, nullptr, nullptr, nullptr, le - lb);
+            } else {
+                for (int64_t i = lb; i < le; ++i) {
+                    if (J.kind == TF_JOB_DOT) {
+                        const tf::d2 p = tf::apply(tf::OP_MUL, J.xh[i], xd ? 0.0 : J.xl[i], xd, J.yh[i],
+                                                   yd ? 0.0 : J.yl[i], yd);
+                        acc = tf::atf1(acc.z0, acc.z1, p.z0, p.z1);
+                    } else {
+                        acc = tf::atf1(acc.z0, acc.z1, J.xh[i], J.xl[i]);
+                    }
                 }
             }
             s0[t] = acc.z0;

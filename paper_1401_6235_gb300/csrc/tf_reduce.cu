@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "tf_host.cuh"
+#include "tf_leaf.cuh"
 
 namespace {
 
@@ -73,12 +74,6 @@ __device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_grou
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-// Four consecutive doubles from a 16-byte aligned address, as two 16-byte loads.
-__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
-    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-
 // One element of a leaf: acc = ATF1(acc, term) (ATF1.1 for a dotted sum).
 template <bool DOT, bool PLAIN>
 __device__ __forceinline__ void leaf_step(tf::d2 &acc, double x0, double x1, bool xd, double y0, double y1,
@@ -115,11 +110,10 @@ __device__ __forceinline__ void write_result(const RedArgs &A, int j, tf::d2 r) 
 // leaf t's row (used by the memory-bound plain twin); otherwise thread t
 // reads its leaf straight from global memory through L1 (the twofold step
 // is compute-bound and barrier-free this way).
-// The twofold (not STAGED) kernel is specialised on the operand kinds KD
-// (bit 0: x dotted, bit 1: y dotted or no y), so its leaf step has no
-// run-time dispatch; when every array's leaf starts on a 16-byte boundary
-// (L even, aligned arrays: uniform over a CTA) it reads 16-byte pairs, four
-// elements per step, and the ragged end of the leaf one element at a time.
+// The twofold (not STAGED) kernel walks its leaves with tf::leaf_walk,
+// specialised on the operand kinds KD (bit 0: x dotted, bit 1: y dotted or
+// no y); with L even and aligned arrays every leaf of a CTA takes its
+// 16-byte loads.
 template <bool DOT, bool PLAIN, bool STAGED, int KD = 3>
 __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant__ RedArgs A) {
     extern __shared__ double stage[];                // [2][narr][B][C+1] when STAGED
@@ -139,27 +133,12 @@ __global__ void __launch_bounds__(kThreads) reduce_blocks(const __grid_constant_
     const int64_t llen = t < nl ? min(A.L, end - lb) : 0;
     const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
     tf::d2 acc = {0.0, 0.0};
-    if (!STAGED) {
+    if constexpr (!STAGED) {
+        static_assert(!PLAIN, "the plain twin stages its leaves");
         constexpr bool XD = (KD & 1) != 0, YD = (KD & 2) != 0;
-        const double *X = A.xh + lb, *XL = XD ? nullptr : A.xl + lb;
-        const double *Y = DOT ? A.yh + lb : nullptr, *YL = (DOT && !YD) ? A.yl + lb : nullptr;
-        int64_t i = 0;
-        const bool vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(XL) |
-                           reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(YL)) & 15) == 0;
-        if (!PLAIN && vec) {
-            for (; i + 4 <= llen; i += 4) {
-                double x[4], xl[4] = {0.0, 0.0, 0.0, 0.0}, y[4] = {0.0, 0.0, 0.0, 0.0}, yl[4] = {0.0, 0.0, 0.0, 0.0};
-                ld4(X + i, x);
-                if (!XD) ld4(XL + i, xl);
-                if (DOT) ld4(Y + i, y);
-                if (DOT && !YD) ld4(YL + i, yl);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) leaf_step<DOT, PLAIN>(acc, x[u], xl[u], XD, y[u], yl[u], YD);
-            }
-        }
-        for (; i < llen; ++i)
-            leaf_step<DOT, PLAIN>(acc, X[i], XD ? 0.0 : XL[i], XD, DOT ? Y[i] : 0.0, (DOT && !YD) ? YL[i] : 0.0,
-                                  YD);
+        if (llen > 0)
+            acc = tf::leaf_walk<DOT, XD, YD>(A.xh + lb, XD ? nullptr : A.xl + lb, DOT ? A.yh + lb : nullptr,
+                                             (DOT && !YD) ? A.yl + lb : nullptr, llen);
     } else {
         const int B = A.B, C = A.C, S = C + 1, narr = A.narr;
         const double *src[4] = {nullptr, nullptr, nullptr, nullptr};

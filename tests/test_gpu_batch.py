@@ -85,6 +85,27 @@ def test_batch_equals_single_job_calls():
             assert np.array_equal(u.cpu().numpy().view(np.uint8), v.cpu().numpy().view(np.uint8)), i
 
 
+def test_jobs_on_unaligned_views():
+    """Dotted sum and dot jobs that are views into one buffer at even and odd
+    element offsets (16-byte and one-element leaf walks in one launch)."""
+    rng = np.random.default_rng(31)
+    x, y = synth.dot_uniform(2_000_003, seed=31)
+    gx, gy = dev(x), dev(y)
+    jobs, ref, a = [], [], 0
+    for j, n in enumerate([100003, 65536, 1, 257, 300000, 4097, 1 << 20, 77]):
+        a += int(rng.integers(0, 3))
+        if j % 2:
+            jobs.append(B.dot_job(gx[a:a + n], gy[a + 1:a + 1 + n]))
+            e0, e1 = O.reduce(x[a:a + n], None, y[a + 1:a + 1 + n], None, L=256)
+        else:
+            jobs.append(B.sum_job(gx[a:a + n]))
+            e0, e1 = O.reduce(x[a:a + n], None, L=256)
+        ref.append(([e0], [e1], [O.flag(e0, e1)]))
+        a += n
+    B.Batch(jobs).launch()
+    check(jobs, ref, "views")
+
+
 def test_relaunch_and_graph_replay():
     """The kernel leaves its counters zeroed: the same plan launched again,
     and replayed from a captured graph, gives the same bits."""

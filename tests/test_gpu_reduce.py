@@ -57,6 +57,49 @@ def test_sum_sizes(n, dotted):
         assert_bits(T.plain_sum(dev(x)), [O.reduce_plain(x)], "plain")
 
 
+@pytest.mark.parametrize("kinds", ["dd", "tt", "td", "dt", "s", "st"])
+@pytest.mark.parametrize("shift", [(1, 1), (0, 1), (1, 0)])
+def test_throughput_schedule_unaligned_leaves(kinds, shift):
+    """The throughput schedule reads a leaf's elements as 16-byte pairs only
+    when every array of the leaf starts on a 16-byte boundary.  Views one
+    element into their allocations (8 bytes off) take the one-element walk,
+    alone or mixed with aligned arrays; every kind of operand, ragged tail."""
+    n = 600011
+    sx, sy = shift
+    x, y = synth.dot_uniform(n + 1, seed=17)
+    xt, yt = tails(x, 5), tails(y, 6)
+    gx, gy, gxt, gyt = dev(x), dev(y), dev(xt), dev(yt)
+    vx, vy = x[sx:sx + n], y[sy:sy + n]
+    use_xl = kinds in ("tt", "td", "st")
+    use_yl = kinds in ("tt", "dt")
+    xl = xt[sx:sx + n] if use_xl else None
+    yl = yt[sy:sy + n] if use_yl else None
+    dgx, dgy = gx[sx:sx + n], gy[sy:sy + n]
+    dxl = gxt[sx:sx + n] if use_xl else None
+    dyl = gyt[sy:sy + n] if use_yl else None
+    if kinds.startswith("s"):
+        e0, e1 = O.reduce(vx, xl, L=256)
+        z0, z1, fl = T.twofold_sum(dgx, dxl)
+    else:
+        e0, e1 = O.reduce(vx, xl, vy, yl, L=256)
+        z0, z1, fl = T.twofold_dot(dgx, dgy, dxl, dyl)
+    assert_bits(z0, [e0], f"{kinds} {shift} z0")
+    assert_bits(z1, [e1], f"{kinds} {shift} z1")
+    assert_flags(fl, [O.flag(e0, e1)], f"{kinds} {shift} flag")
+
+
+def test_throughput_schedule_jobs_of_both_parities():
+    """Batched jobs that start on even and odd elements: within one launch
+    some CTAs take the 16-byte walk and some the one-element walk."""
+    x, y = synth.dot_uniform(1_500_007, seed=23)
+    offs = np.array([0, 300001, 600002, 900004, 1200005, 1500007], np.int64)
+    r0, r1, rf = O.dot_batched(x, None, y, None, offs)
+    z0, z1, fl = T.twofold_dot_batched(dev(x), dev(y), offs)
+    assert_bits(z0, r0, "z0")
+    assert_bits(z1, r1, "z1")
+    assert_flags(fl, rf, "flags")
+
+
 @pytest.mark.parametrize("L", [1, 3, 7, 64, 1000, 1 << 20])
 def test_leaf_sizes(L):
     n = 300007
