@@ -61,7 +61,7 @@ HORNER_OPS_PER_STEP = 4 + 7              # MTF1.1 + ATF1.1
 # profiles/), scaled by the units a launch processes; None where the kernel
 # changed after its counters were taken.
 TRAFFIC_PER_UNIT = {
-    "ew_chain": ((279.619e6 + 83.100e6) * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
+    "ew_chain": ((281.741e6 + 85.110e6) * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
     "ew_chain_f32": ((536.964e6 + 130.670e6) * 16 / (1 << 28), "profiles/tf_jit_ew_chain_f32_n2e28.md"),
     "horner": (1.571e9 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
     "cond_dots": ((268.51e6 + 3.47e6) / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
@@ -75,7 +75,7 @@ TRAFFIC_PER_UNIT = {
 # pipes, so the alu roofline's frac (algorithmic FP64 operations against the
 # FP64 pipe alone) can exceed 1 while neither pipe is full.
 PIPES = {
-    "ew_chain": ({"fp64": 0.745, "alu": 0.695, "issue": 0.615}, "profiles/tf_jit_ew_chain_n2e28.md"),
+    "ew_chain": ({"fp64": 0.745, "alu": 0.719, "issue": 0.632}, "profiles/tf_jit_ew_chain_n2e28.md"),
     "horner": ({"fp64": 0.808, "alu": 0.774, "issue": 0.591}, "profiles/horner_kernel_k5-30_2e24.md"),
     "cond_dots": ({"fp64": 0.290, "alu": 0.444, "issue": 0.330}, "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
     "dot": ({"fp64": 0.252, "alu": 0.081}, "profiles/reduce_lat_dot_n65536.md"),

@@ -33,8 +33,10 @@
 
 #if defined(__CUDACC__)
 #define TFS_HD __host__ __device__ __forceinline__
+#define TFS_COLD static __host__ __device__ __noinline__   // rare paths: kept out of the hot code
 #else
 #define TFS_HD inline
+#define TFS_COLD static inline
 #endif
 
 namespace tf {
@@ -546,24 +548,36 @@ TFS_HD double add_rn(double a, double b) {
 // remainder finishes as in sqrt_rn_y.  Otherwise the full routine runs.
 // With rem != nullptr, *rem also receives RN(u - v^2) for the returned root
 // v, the bits of fma(-v, v, u) (Algorithm 5's exact residual).
+// The general case of sqrt_rn_near (u far from x, or a special value):
+// the full root, and its residual where rem is wanted.
+TFS_COLD double sqrt_near_general(double u, double *rem) {
+    const uint64_t uu = d2u(u);
+    uint64_t y;
+    const double v = sqrt_rn_y(u, &y);
+    if (rem) {
+        // fma(-v, v, u) without a native operation where the root is NaN
+        // (NaN), +Inf (-Inf + Inf: NaN) or a zero (v = u, -u u + u = u)
+        const uint64_t xu = uu & ~kSign, inf = 0x7FF0000000000000ull;
+        if ((uu >> 63 && xu != 0) || xu >= inf) *rem = u2d(0x7FF8000000000000ull);
+        else if (xu == 0) *rem = u;
+        else *rem = native_fma(u2d(d2u(v) ^ kSign), v, u);
+    }
+    return v;
+}
+
 TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx, double *rem = nullptr) {
     const uint64_t uu = d2u(u), ux = d2u(x);
+    // a negative radicand or a NaN with the sign bit set: NaN root and
+    // residual, resolved here because they are common (a chain whose value
+    // went negative) while the general case below is rare
+    if ((uu >> 63) && (uu << 1)) {
+        if (rem) *rem = u2d(0x7FF8000000000000ull);
+        return u2d(0x7FF8000000000000ull);
+    }
     const int f = (int)(uu >> 52);
     const uint64_t mu = (uu & kFrac) | kHid, mx = (ux & kFrac) | kHid;
     const uint64_t diff = mu > mx ? mu - mx : mx - mu;
-    if (yx == 0 || f != (int)(ux >> 52) || (unsigned)(f - 1) >= 2046u || diff > 256) {
-        uint64_t y;
-        const double v = sqrt_rn_y(u, &y);
-        if (rem) {
-            // fma(-v, v, u) without a native operation where the root is NaN
-            // (NaN), +Inf (-Inf + Inf: NaN) or a zero (v = u, -u u + u = u)
-            const uint64_t xu = uu & ~kSign, inf = 0x7FF0000000000000ull;
-            if ((uu >> 63 && xu != 0) || xu >= inf) *rem = u2d(0x7FF8000000000000ull);
-            else if (xu == 0) *rem = u;
-            else *rem = native_fma(u2d(d2u(v) ^ kSign), v, u);
-        }
-        return v;
-    }
+    if (yx == 0 || f != (int)(ux >> 52) || (unsigned)(f - 1) >= 2046u || diff > 256) return sqrt_near_general(u, rem);
     const int odd = f & 1;
     const int s = odd ? 52 : 53;
     const uint64_t m_hi = mu >> (64 - s), m_lo = mu << s;
