@@ -66,7 +66,7 @@ TRAFFIC_PER_UNIT = {
     "horner": (1.571e9 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
     "cond_dots": ((268.51e6 + 3.47e6) / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
     "dot": (1.120256e6 / 65536, "profiles/reduce_lat_dot_n65536.md"),
-    "dot_f32": ((268.462e6 + 3.952e6) / (1 << 25), "profiles/red32_blocks_dot_f32_2e28.md"),
+    "dot_f32": ((536.895e6 + 3.582e6) / (1 << 26), "profiles/red32_blocks_dot_f32_2e28.md"),
 }
 
 # ncu pipe activity of the dominant kernel (fraction of its peak sustained

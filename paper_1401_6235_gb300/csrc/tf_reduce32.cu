@@ -265,28 +265,50 @@ __global__ void __launch_bounds__(kThreads32) red32_blocks_v4(const __grid_const
     }
 }
 
-// One CTA: thread t first folds the aligned group of G partials [tG,
-// (t+1)G) in place (G = 2^g, G kThreads32 >= nblk), a subtree, then the CTA
-// reduces the group roots.
+// One CTA of kFinal32 threads: thread t first folds the aligned group of G
+// partials [tG, (t+1)G) (G = 2^g, G kFinal32 >= nblk), a subtree, then the
+// CTA reduces the group roots.  Groups of up to 8 partials are loaded
+// together (32 contiguous bytes per thread and array) and folded in
+// registers; larger groups fold in place in the workspace.
+constexpr int kFinal32 = 1024;
+
 template <bool PLAIN>
-__global__ void __launch_bounds__(kThreads32) red32_final(const __grid_constant__ Red32Args A) {
-    __shared__ float s0[kThreads32], s1[kThreads32];
+__global__ void __launch_bounds__(kFinal32) red32_final(const __grid_constant__ Red32Args A) {
+    __shared__ float s0[kFinal32], s1[kFinal32];
     const int t = threadIdx.x;
     const int64_t nb = A.nblk;
     int64_t G = 1;
-    while (G * kThreads32 < nb) G <<= 1;
+    while (G * kFinal32 < nb) G <<= 1;
     const int ng = (int)((nb + G - 1) / G);
     if (t < ng) {
         float *q0 = A.part0 + (int64_t)t * G, *q1 = A.part1 + (int64_t)t * G;
         const int64_t cnt = min(G, nb - (int64_t)t * G);
-        for (int64_t s = 1; s < cnt; s <<= 1)
-            for (int64_t i = 0; i + s < cnt; i += 2 * s) {
-                const tf::f2 r = combine32<PLAIN>({q0[i], q1[i]}, {q0[i + s], q1[i + s]});
-                q0[i] = r.z0;
-                q1[i] = r.z1;
-            }
-        s0[t] = q0[0];
-        s1[t] = q1[0];
+        if (G <= 8) {
+            float r0[8], r1[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < cnt) { r0[i] = q0[i]; r1[i] = q1[i]; }
+#pragma unroll
+            for (int st = 1; st < 8; st <<= 1)
+#pragma unroll
+                for (int i = 0; i + st < 8; i += 2 * st)
+                    if (i + st < cnt) {
+                        const tf::f2 r = combine32<PLAIN>({r0[i], r1[i]}, {r0[i + st], r1[i + st]});
+                        r0[i] = r.z0;
+                        r1[i] = r.z1;
+                    }
+            s0[t] = r0[0];
+            s1[t] = r1[0];
+        } else {
+            for (int64_t st = 1; st < cnt; st <<= 1)
+                for (int64_t i = 0; i + st < cnt; i += 2 * st) {
+                    const tf::f2 r = combine32<PLAIN>({q0[i], q1[i]}, {q0[i + st], q1[i + st]});
+                    q0[i] = r.z0;
+                    q1[i] = r.z1;
+                }
+            s0[t] = q0[0];
+            s1[t] = q1[0];
+        }
     }
     __syncthreads();
     smem_tree32<PLAIN>(s0, s1, ng);
@@ -329,14 +351,25 @@ int run32(const float *xh, const float *xl, const float *yh, const float *yl, in
     A.n = n;
     A.L = tfh::leaf_of(p);
     const int64_t M = (n + A.L - 1) / A.L;
-    // staged arrays; leaves per block: at most what two chunk buffers of all
-    // arrays fit in shared memory, and at least ~1024 blocks while B >= 1
+    // staged arrays; leaves per block B: at most what leaves three CTAs'
+    // double buffers of all arrays room in shared memory (more resident warps
+    // hide the leaves' dependent chains: a 2^28-element dotted dot took
+    // 0.355 ms at B = 128, three CTAs per SM, against 0.428 ms at B = 256,
+    // one), and at least ~1024 blocks while B >= 1; then larger (up to one
+    // CTA per SM) where the caller's workspace would not hold the partials
     const int narr = 1 + (!PLAIN && xl != nullptr) + (DOT ? 1 + (!PLAIN && yl != nullptr) : 0);
     auto tile_bytes = [&](int b) { return 2 * (size_t)narr * b * (kChunk32 + 1) * sizeof(float); };
-    int Bmax = kThreads32;
-    while (Bmax > 1 && tile_bytes(Bmax) > 227 * 1024) Bmax >>= 1;
+    constexpr size_t kSmem = 227 * 1024;
+    int Bfit = kThreads32, Bocc = kThreads32;
+    while (Bfit > 1 && tile_bytes(Bfit) > kSmem) Bfit >>= 1;
+    while (Bocc > 1 && 3 * tile_bytes(Bocc) > kSmem) Bocc >>= 1;
     int B = 1;
-    while (B < Bmax && (int64_t)B * 2 * 1024 <= M) B <<= 1;
+    while (B < Bocc && (int64_t)B * 2 * 1024 <= M) B <<= 1;
+    auto ws_need = [&](int b) {
+        const int64_t nb = (M + b - 1) / b;
+        return nb > 1 ? 2 * al256(sizeof(float) * (size_t)nb) : (size_t)0;
+    };
+    while (B < Bfit && ws_need(B) > ws_bytes) B <<= 1;
     A.B = B;
     A.nblk = (M + B - 1) / B;
     if (A.nblk > 0x7FFFFFFFLL) return TF_EUNSUPPORTED;
@@ -361,7 +394,7 @@ int run32(const float *xh, const float *xl, const float *yh, const float *yl, in
                                 cudaSuccess)
         return TF_ECUDA;
     kern<<<(unsigned)A.nblk, threads, smem, s>>>(A);
-    if (A.nblk > 1) red32_final<PLAIN><<<1, kThreads32, 0, s>>>(A);
+    if (A.nblk > 1) red32_final<PLAIN><<<1, kFinal32, 0, s>>>(A);
     return tfh::launch_status();
 }
 

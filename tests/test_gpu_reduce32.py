@@ -122,6 +122,24 @@ def test_dot32_large_both_tails_exact_workspace():
     assert_flags(fl, [O.flag32(r0, r1)], "flag")
 
 
+def test_dot32_small_workspace_takes_larger_blocks():
+    """2^26 dotted elements (2^18 leaves) in a workspace that holds the
+    partials of 256-leaf blocks but not of the preferred 128-leaf blocks:
+    the call takes the larger blocks, with the oracle's bits; a workspace
+    too small for those too is refused."""
+    import torch
+    n = 1 << 26
+    x, y = data32(n, 91)
+    ws = torch.empty(2 * 4096, dtype=torch.uint8, device="cuda")    # two arrays of 1024 floats
+    z0, z1, fl = T.twofold_dot_f32(dev(x), dev(y), ws=ws)
+    r0, r1 = O.reduce32(x, None, y, None)
+    assert_bits32(z0, np.float32([r0]), "z0")
+    assert_bits32(z1, np.float32([r1]), "z1")
+    assert_flags(fl, [O.flag32(r0, r1)], "flag")
+    with pytest.raises(T.TwofoldError):
+        T.twofold_dot_f32(dev(x), dev(y), ws=ws[:4096])
+
+
 def test_dot32_full_size_bench_configuration():
     """The binary32 dot workload at full size: 2^28 dotted elements, uniform
     [-1, 1] floats of seed 0, the benchmark's call; the whole result against
