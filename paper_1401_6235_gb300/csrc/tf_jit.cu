@@ -62,13 +62,15 @@ std::string key_of(const Prog &p) {
 
 bool unary(int op) { return op == TF_SQRT || op == TF_PSQRT; }
 
-// Register budget of the binary64 kernels, as CTAs of 128 per SM: a short
-// program (the chain shape: up to 4 inputs, 8 instructions) runs at full
-// occupancy, 16 CTAs (32 registers, a little spill to L1: the sqrt((a*b+c)/d)
-// chain measured 3.6 % faster than with 12); longer programs keep 12
-// (40 registers); binary32 takes the compiler's choice.
+// Register budget as CTAs of 128 per SM, measured on the sqrt((a*b+c)/d)
+// chain over 2^28 elements.  binary64: a short program (the chain shape: up
+// to 4 inputs, 8 instructions) runs at full occupancy, 16 CTAs (32
+// registers, a little spill to L1: 3.6 % faster than 12); longer programs
+// keep 12 (40 registers).  binary32 (two elements per thread): the twofold
+// kernel at 8 (1.80 ms against 1.83 with the compiler's choice, 1.91 at
+// 12), the plain twin at 16 (0.85 ms against 0.97).
 std::string min_blocks(const Prog &p) {
-    if (p.is_f32) return "";
+    if (p.is_f32) return p.plain ? ", 16" : ", 8";
     return p.nin <= 4 && p.nprog <= 8 ? ", 16" : ", 12";
 }
 
