@@ -11,10 +11,11 @@ lists the readings taken where the paper is silent or misprinted.
 
 Pinned by ``tests/test_oracle_*.py`` against exact rational arithmetic, the
 paper's worked examples and printed application logs, closed forms and
-special-case reductions.  One part stays "parity unpinned" beyond examples:
-RTF1 for non-coupled input (the paper gives no error bound); it is pinned by
-the worked example of the Root section and by loose closeness to a
-high-precision square root.
+special-case reductions.  The paper states no error bound for RTF1; its pin
+is a bound derived from its own steps (the exact remainder of the
+first-order root correction plus one rounding per step), checked against a
+high-precision square root for coupled and non-coupled inputs, besides the
+Root section's worked example.
 """
 from __future__ import annotations
 

@@ -8,7 +8,8 @@
 * the worked examples of the Add/subtract, Divide and Root sections;
 * rounding-error budgets of the general algorithms derived from their exact
   expansions (dz0 = x1 + y1 + e for ATF1, e00 + x0y1 + x1y0 + x1y1 for MTF1,
-  (x - z0 y)/y for DTF1), with tails spread over the epsilon-order regimes so
+  (x - z0 y)/y for DTF1, the first-order root correction of RTF1 with its
+  exact remainder term), with tails spread over the epsilon-order regimes so
   that a dropped term, a wrong sign or a swapped operand exceeds the budget.
 """
 import math
@@ -242,9 +243,8 @@ def test_dtf11_budget(data):
 
 
 def test_rtf1_coupled_loose(data):
-    """RTF1 has no error bound in the paper (parity unpinned beyond the
-    worked example); for coupled input z0 + z1 must be close to the exact
-    root: |dz1| <= 8 u^2 |z0| + 2 u |z1|."""
+    """Coupled input (|x1| below half an ulp of x0): z0 + z1 is close to the
+    exact root, |dz1| <= 8 u^2 |z0| + 2 u |z1|."""
     x0, _, _, _ = data
     rng = np.random.default_rng(5)
     a0s = np.abs(x0)
@@ -257,16 +257,51 @@ def test_rtf1_coupled_loose(data):
         assert abs(err) <= 8 * U * U * F(z0) + 2 * U * abs(F(z1)), (a0, a1)
 
 
-def test_rtf1_non_coupled_follows_rpf_of_renormalised(data):
-    """For non-coupled input RTF1 approximates sqrt(x0 + x1) - z0 through
-    the renormalised (u0, u1): z0 + z1 within 4 u |sqrt(x)| (loose)."""
-    rng = np.random.default_rng(6)
-    a0s = np.abs(data[0][:500])
-    a1s = a0s * (rng.random(a0s.size) * 2 - 1) * 0.5
+def rtf1_inputs():
+    """x0 > 0 with tails of every size: coupled (below half an ulp), spread
+    over the epsilon-order regimes, up to half of x0 and up to nine times
+    it (where v0 and z0 are more than a factor 2 apart and Two-Diff's tail
+    is not zero)."""
+    rng = np.random.default_rng(7)
+    a0 = np.abs(rand_doubles(rng, 4000, -30, 30))
+    a1 = np.concatenate([(rng.random(1000) - 0.5) * np.array([ulp(v) for v in a0[:1000]]),
+                         rand_tails(rng, a0[1000:2000], 1, 70),
+                         a0[2000:3000] * (rng.random(1000) - 0.5),
+                         a0[3000:] * rng.uniform(-0.9, 9.0, 1000)])
+    return a0, a1
+
+
+def test_rtf1_budget():
+    """The Root section's RTF1 step by step, each rounding bounded (u = 2^-53,
+    |RN(a) - a| <= u |RN(a)|):
+      z0 = RN(sqrt x0);  (u0, u1) = Two-Sum(x0, x1), so u0 + u1 = x0 + x1 = X;
+      RPF1: v0 = RN(sqrt u0), d = u0 - v0^2 exactly (Algorithm 5),
+            c = RN(u1 + d), v1 = RN(c / (2 v0));
+      STF1.1: w0 = RN(v0 - z0) with the exact tail e, w1 = RN(v1 + e);
+      z1 = RN(w0 + w1).
+    With delta = u1 + d = X - v0^2 and s = sqrt(X), the identity
+    s - v0 - delta/(2 v0) = -delta^2 / (2 v0 (s + v0)^2) gives
+      z0 + z1 - s = delta^2/(2 v0 (s + v0)^2) + rho_c/(2 v0) + rho_v1 + rho_w1 + rho_z1,
+    so |z0 + z1 - s| <= delta^2/(2 v0 (s + v0)^2) + u |c|/(2 v0) + u (|v1| + |w1| + |z1|).
+    Checked against the exact root of the exact input (300 bits)."""
+    a0s, a1s = rtf1_inputs()
     for a0, a1 in zip(a0s, a1s):
         z0, z1 = O.rtf1(a0, a1)
-        exact = isqrt_frac(F(a0) + F(a1))
-        assert abs(F(z0) + F(z1) - exact) <= 4 * U * exact, (a0, a1)
+        assert same(z0, math.sqrt(a0))
+        X = F(a0) + F(a1)
+        s = isqrt_frac(X)
+        u0, u1 = O.two_sum(a0, a1)
+        v0 = math.sqrt(u0)
+        d = fma(-v0, v0, u0)
+        c = u1 + d
+        v1 = c / (2.0 * v0)
+        w0, e = O.two_diff(v0, z0)
+        w1 = v1 + e
+        delta = X - F(v0) * F(v0)
+        model = delta * delta / (2 * F(v0) * (s + F(v0)) ** 2)
+        budget = model + U * (abs(F(c)) / (2 * F(v0)) + abs(F(v1)) + abs(F(w1)) + abs(F(z1)))
+        err = F(z0) + F(z1) - s
+        assert abs(err) <= budget * (1 + Fraction(1, 2 ** 40)) + s * Fraction(1, 2 ** 290), (a0, a1, float(err))
 
 
 # --------------------------------------------------------------- panic flag

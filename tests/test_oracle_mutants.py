@@ -62,7 +62,12 @@ MUTANTS = {
     "rpf11_no_factor_two": (("tfo_rpf11", "double w = 2.0 * c;", "double w = c;"),
                             [lambda: TA.test_rpf11_output_coupled(data())]),
     "rtf1_drops_u1": (("tfo_rtf1", "tfo_rpf1(u0, u1)", "tfo_rpf1(u0, 0.0)"),
-                      [lambda: TA.test_rtf1_coupled_loose(data())]),
+                      [lambda: TA.test_rtf1_coupled_loose(data()), TA.test_rtf1_budget]),
+    "rtf1_input_tail_for_two_sum_tail": (("tfo_rtf1", "tfo_rpf1(u0, u1)", "tfo_rpf1(u0, x1)"),
+                                         [TA.test_rtf1_budget]),
+    "rtf1_drops_w1": (("tfo_rtf1", "z.z1 = w.z0 + w.z1;", "z.z1 = w.z0;"), [TA.test_rtf1_budget]),
+    "rtf1_stf_operands_swapped": (("tfo_rtf1", "tfo_stf11(v.z0, v.z1, z0)", "tfo_stf11(z0, v.z1, v.z0)"),
+                                  [TA.test_rtf1_budget]),
     "two_sum_swaps_roles": (("tfo_two_sum", "double b1 = s_ - a;", "double b1 = s_ - b;"),
                             [lambda: TT.test_two_sum_exact(TT.make_pairs())]),
     "leaf_skips_first": (("leaf_reduce", "for (int64_t i = b; i < e; ++i)",
