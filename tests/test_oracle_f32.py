@@ -3,7 +3,9 @@ variants against exact rational arithmetic rounded to binary32, the float
 rows of the paper's application logs (tests/golden/paper_logs.txt: gauss
 well3 / ill3, test100h, quadratic, and the float conversions of their
 inputs), the renormalising accumulator of the Applications section in the
-paper's own binary24 format, and the sticky flag."""
+paper's own binary24 format, the sticky flag, and rounding-error budgets of
+the general add, subtract, multiply, divide and root derived from their
+steps (the binary64 tests' derivations with u = 2^-24)."""
 import math
 from fractions import Fraction
 
@@ -99,6 +101,80 @@ def test_dtf111_and_rpf11_32(pairs):
         assert abs(c1) <= ulp32(c0) / 2
         dz0 = isqrt_frac(abs(F(x))) - F(c0)
         assert abs(F(c1) - dz0) <= 4 * U32 * abs(F(c1)) + F(c0) * U32 * U32 * 4
+
+
+def _tailed(rng, heads, kmin, kmax):
+    """binary32 tails |x1| ~ |x0| 2^-k, k uniform in [kmin, kmax]."""
+    return np.array([f32(h * 2.0 ** -int(rng.integers(kmin, kmax + 1)) * rng.uniform(-1, 1)) for h in heads])
+
+
+def _ok32(err, budget):
+    return abs(err) <= budget * (1 + Fraction(1, 2 ** 20)) + Fraction(1, 2 ** 149)
+
+
+def test_mtf1_budget32(pairs):
+    """General twofold multiply: dz0 = e00 + x0 y1 + x1 y0 + x1 y1 exactly;
+    the formula rounds the three products and three sums once each."""
+    a, b = (v[:6000] for v in pairs)
+    rng = np.random.default_rng(10)
+    x1s, y1s = _tailed(rng, a, 1, 30), _tailed(rng, b, 1, 30)
+    for x0, x1, y0, y1 in zip(a, x1s, b, y1s):
+        z0, z1 = O.op32(O.MUL, (x0, x1), (y0, y1))
+        assert z0 == rn32(F(x0) * F(y0))
+        dz0 = (F(x0) + F(x1)) * (F(y0) + F(y1)) - F(z0)
+        _, e00 = O.two_prod32(x0, y0)
+        p11, p01, p10 = rn32(F(x1) * F(y1)), rn32(F(x0) * F(y1)), rn32(F(x1) * F(y0))
+        s1, s2 = rn32(F(e00) + F(p11)), rn32(F(p01) + F(p10))
+        budget = U32 * sum(abs(F(v)) for v in (p11, p01, p10, s1, s2, z1))
+        assert _ok32(F(z1) - dz0, budget), (x0, x1, y0, y1)
+
+
+def test_dtf1_budget32(pairs):
+    """General twofold divide: x - z0 y = r0 + (x1 - z0 y1) with r0 exact;
+    z1 = RN(RN(r0 + RN(x1 - z0 y1)) / RN(y0 + y1)).  Budget: the rounding of
+    the remainder's two terms, of the denominator and of the quotient."""
+    a, b = (v[:6000] for v in pairs)
+    rng = np.random.default_rng(11)
+    x1s, y1s = _tailed(rng, a, 1, 30), _tailed(rng, b, 1, 30)
+    for x0, x1, y0, y1 in zip(a, x1s, b, y1s):
+        z0, z1 = O.op32(O.DIV, (x0, x1), (y0, y1))
+        assert z0 == rn32(F(x0) / F(y0))
+        y = F(y0) + F(y1)
+        dz0 = (F(x0) + F(x1)) / y - F(z0)
+        _, r0 = O.div_rem32(x0, y0)
+        r1 = rn32(F(x1) - F(z0) * F(y1))
+        c0, d0 = rn32(F(r0) + F(r1)), rn32(F(y0) + F(y1))
+        q = F(c0) / F(d0)
+        budget = U32 * abs(F(z1)) + abs(q) * abs(y - F(d0)) / abs(y) + U32 * (abs(F(r1)) + abs(F(c0))) / abs(y)
+        assert _ok32(F(z1) - dz0, budget), (x0, x1, y0, y1)
+
+
+def test_rtf1_budget32(pairs):
+    """Twofold root, its steps in binary32 with the binary64 test's
+    derivation: Two-Sum (exact), RPF1 on (u0, u1) with the exact residual d
+    and the exact remainder delta^2 / (2 v0 (s + v0)^2) of the first-order
+    correction (delta = u1 + d), STF1.1 against z0, one rounding per step;
+    tails from below half an ulp to nine times x0."""
+    a = np.abs(pairs[0][:6000])
+    rng = np.random.default_rng(12)
+    x1s = np.concatenate([_tailed(rng, a[:2000], 25, 40), _tailed(rng, a[2000:4000], 1, 24),
+                          np.array([f32(h * rng.uniform(-0.9, 9.0)) for h in a[4000:]])])
+    for x0, x1 in zip(a, x1s):
+        z0, z1 = O.op32(O.SQRT, (x0, x1))
+        assert z0 == rn32(isqrt_frac(F(x0), 80))
+        X = F(x0) + F(x1)
+        s = isqrt_frac(X)
+        u0, u1 = O.two_sum32(x0, x1)
+        v0, d = O.sqrt_rem32(u0)
+        c = rn32(F(u1) + F(d))
+        v1 = rn32(F(c) / (2 * F(v0)))
+        _, e = O.two_diff32(v0, z0)
+        w1 = rn32(F(v1) + F(e))
+        delta = X - F(v0) * F(v0)
+        model = delta * delta / (2 * F(v0) * (s + F(v0)) ** 2)
+        budget = model + U32 * (abs(F(c)) / (2 * F(v0)) + abs(F(v1)) + abs(F(w1)) + abs(F(z1)))
+        err = F(z0) + F(z1) - s
+        assert _ok32(err, budget), (x0, x1, float(err), float(budget))
 
 
 # --------------------------------------------------------------- paper logs

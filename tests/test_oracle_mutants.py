@@ -48,6 +48,11 @@ def data():
     return DATA
 
 
+def _pairs32():
+    rng = __import__("numpy").random.default_rng(32)
+    return TF.rand32(rng, 6000), TF.rand32(rng, 6000)
+
+
 MUTANTS = {
     "mtf1_drops_p11": (("tfo_mtf1", "double u = e00 + p11;", "double u = e00;"),
                        [lambda: TA.test_mtf1_budget(data())]),
@@ -100,6 +105,12 @@ MUTANTS = {
                                    [lambda: TF.test_exact_transforms32(
                                        (TF.rand32(__import__("numpy").random.default_rng(1), 3000),
                                         TF.rand32(__import__("numpy").random.default_rng(2), 3000)))]),
+    "f32_mtf1_drops_p11": (("tfof_mtf1", "float u = e00 + p11;", "float u = e00;"),
+                           [lambda: TF.test_mtf1_budget32(_pairs32())]),
+    "f32_dtf1_r1_sign": (("tfof_dtf1", "fmaf(-q, y1, x1)", "fmaf(q, y1, x1)"),
+                         [lambda: TF.test_dtf1_budget32(_pairs32())]),
+    "f32_rtf1_drops_w1": (("tfof_rtf1", "z.z1 = w.z0 + w.z1;", "z.z1 = w.z0;"),
+                          [lambda: TF.test_rtf1_budget32(_pairs32())]),
     "f32_atf1_subtracts_tail": (("tfof_atf1", "float u = x1 + y1;", "float u = x1 - y1;"),
                                 [lambda: TF.test_atf1_stf1_budget32(
                                     (TF.rand32(__import__("numpy").random.default_rng(1), 3000),
