@@ -63,7 +63,7 @@ HORNER_OPS_PER_STEP = 4 + 7              # MTF1.1 + ATF1.1
 TRAFFIC_PER_UNIT = {
     "ew_chain": ((281.741e6 + 85.110e6) * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
     "ew_chain_f32": ((536.904e6 + 130.459e6) * 16 / (1 << 28), "profiles/tf_jit_ew_chain_f32_n2e28.md"),
-    "horner": (1.571e9 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
+    "horner": ((268.576e6 + 515.401e6) * 2 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
     "cond_dots": ((268.51e6 + 3.47e6) / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
     "dot": (1.120256e6 / 65536, "profiles/reduce_lat_dot_n65536.md"),
     "dot_f32": ((536.895e6 + 3.582e6) / (1 << 26), "profiles/red32_blocks_dot_f32_2e28.md"),
