@@ -11,6 +11,7 @@
 // then an in-place strided tree in shared memory) and reduce_final
 // combines the partials of each job with the same tree.  Results therefore
 // do not depend on B, the grid or the device.
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -74,7 +75,8 @@ __device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_grou
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-// One element of a leaf: acc = ATF1(acc, term) (ATF1.1 for a dotted sum).
+// One element of a leaf: acc = ATF1(acc, term) (ATF1.1 for a dotted sum);
+// the plain twin adds the plain term (separate multiplication and addition).
 template <bool DOT, bool PLAIN>
 __device__ __forceinline__ void leaf_step(tf::d2 &acc, double x0, double x1, bool xd, double y0, double y1,
                                           bool yd) {
@@ -454,12 +456,17 @@ int lat_group(int64_t L, int64_t M) {
 
 size_t lat_smem(int B, int64_t L) { return LatRows(L).bytes(B); }
 
-// One CTA per job with 0 or >= 2 blocks.  Thread t first reduces the aligned
-// group of G partials [tG, (t+1)G) in place (G = 2^g, G*kThreads >= nb),
-// which is a subtree, then the CTA reduces the group roots.
-template <bool PLAIN>
-__global__ void __launch_bounds__(kThreads) reduce_final(const __grid_constant__ RedArgs A) {
-    __shared__ double s0[kThreads], s1[kThreads];
+// One CTA of T threads per job with 0 or >= 2 blocks.  Thread t first
+// reduces the aligned group of G partials [tG, (t+1)G) (G = 2^g,
+// G T >= nb), which is a subtree, then the CTA reduces the group roots.
+// Groups of up to 4 partials are loaded together and folded in registers;
+// larger groups fold in place in the workspace (a dependent global load per
+// step).  T = 256 up to 1024 partials per job, 1024 beyond (launch_final).
+constexpr int kFinalThreads = 1024;
+
+template <bool PLAIN, int T>
+__global__ void __launch_bounds__(T) reduce_final(const __grid_constant__ RedArgs A) {
+    __shared__ double s0[T], s1[T];
     griddep_wait();
     griddep_release();
     const int j = blockIdx.x, t = threadIdx.x;
@@ -473,19 +480,37 @@ __global__ void __launch_bounds__(kThreads) reduce_final(const __grid_constant__
         return;
     }
     int64_t G = 1;
-    while (G * kThreads < nb) G <<= 1;
+    while (G * T < nb) G <<= 1;
     const int ng = (int)((nb + G - 1) / G);
     if (t < ng) {
         double *q0 = A.part0 + p0 + (int64_t)t * G, *q1 = A.part1 + p0 + (int64_t)t * G;
         const int64_t cnt = min(G, nb - (int64_t)t * G);
-        for (int64_t s = 1; s < cnt; s <<= 1)
-            for (int64_t i = 0; i + s < cnt; i += 2 * s) {
-                tf::d2 r = combine<PLAIN>({q0[i], q1[i]}, {q0[i + s], q1[i + s]});
-                q0[i] = r.z0;
-                q1[i] = r.z1;
-            }
-        s0[t] = q0[0];
-        s1[t] = q1[0];
+        if (G <= 4) {
+            double r0[4], r1[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i < cnt) { r0[i] = q0[i]; r1[i] = q1[i]; }
+#pragma unroll
+            for (int st = 1; st < 4; st <<= 1)
+#pragma unroll
+                for (int i = 0; i + st < 4; i += 2 * st)
+                    if (i + st < cnt) {
+                        const tf::d2 r = combine<PLAIN>({r0[i], r1[i]}, {r0[i + st], r1[i + st]});
+                        r0[i] = r.z0;
+                        r1[i] = r.z1;
+                    }
+            s0[t] = r0[0];
+            s1[t] = r1[0];
+        } else {
+            for (int64_t s = 1; s < cnt; s <<= 1)
+                for (int64_t i = 0; i + s < cnt; i += 2 * s) {
+                    tf::d2 r = combine<PLAIN>({q0[i], q1[i]}, {q0[i + s], q1[i + s]});
+                    q0[i] = r.z0;
+                    q1[i] = r.z1;
+                }
+            s0[t] = q0[0];
+            s1[t] = q1[0];
+        }
     }
     __syncthreads();
     for (int s = 1; s < ng; s <<= 1) {
@@ -523,6 +548,14 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Workspace: [offs (njobs+1) | blk0 (njobs+1)] [part0 (nblk)] [part1 (nblk)].
 size_t ws_need(int njobs, int64_t nblk) {
     return align256(sizeof(int64_t) * 2 * (size_t)(njobs + 1)) + 2 * align256(sizeof(double) * (size_t)nblk);
+}
+
+// The final tree's launch, its CTA size chosen by the most partials of a job.
+template <bool PLAIN>
+cudaError_t launch_final(int njobs, int64_t max_partials, cudaStream_t s, const RedArgs &A) {
+    if (max_partials > 4 * kThreads)
+        return tfh::launch_pdl(reduce_final<PLAIN, kFinalThreads>, njobs, kFinalThreads, 0, s, A);
+    return tfh::launch_pdl(reduce_final<PLAIN, kThreads>, njobs, kThreads, 0, s, A);
 }
 
 template <bool DOT, bool PLAIN>
@@ -621,7 +654,9 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
             if (e != cudaSuccess) return TF_ECUDA;
         }
     }
-    if (need_final && tfh::launch_pdl(reduce_final<PLAIN>, njobs, kThreads, 0, s, A) != cudaSuccess)
+    int64_t maxp = 0;                                 // the most partials of one job
+    for (int j = 0; j < njobs; ++j) maxp = std::max(maxp, tab[njobs + 2 + j] - tab[njobs + 1 + j]);
+    if (need_final && launch_final<PLAIN>(njobs, maxp, s, A) != cudaSuccess)
         return TF_ECUDA;
     return tfh::launch_status();
 }
@@ -773,6 +808,6 @@ extern "C" int twofold_combine(const double *z0, const double *z1, int64_t m, tf
             cudaMemcpyAsync(A.part1, z1, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return TF_ECUDA;
     }
-    if (tfh::launch_pdl(reduce_final<false>, 1, kThreads, 0, s, A) != cudaSuccess) return TF_ECUDA;
+    if (launch_final<false>(1, m, s, A) != cudaSuccess) return TF_ECUDA;
     return tfh::launch_status();
 }
