@@ -265,20 +265,21 @@ __global__ void __launch_bounds__(kThreads32) red32_blocks_v4(const __grid_const
     }
 }
 
-// One CTA of kFinal32 threads: thread t first folds the aligned group of G
-// partials [tG, (t+1)G) (G = 2^g, G kFinal32 >= nblk), a subtree, then the
-// CTA reduces the group roots.  Groups of up to 8 partials are loaded
-// together (32 contiguous bytes per thread and array) and folded in
-// registers; larger groups fold in place in the workspace.
+// One CTA of T threads: thread t first folds the aligned group of G
+// partials [tG, (t+1)G) (G = 2^g, G T >= nblk), a subtree, then the CTA
+// reduces the group roots.  Groups of up to 8 partials are loaded together
+// (32 contiguous bytes per thread and array) and folded in registers;
+// larger groups fold in place in the workspace.  T = 256 up to 2048
+// partials, 1024 beyond.
 constexpr int kFinal32 = 1024;
 
-template <bool PLAIN>
-__global__ void __launch_bounds__(kFinal32) red32_final(const __grid_constant__ Red32Args A) {
-    __shared__ float s0[kFinal32], s1[kFinal32];
+template <bool PLAIN, int T>
+__global__ void __launch_bounds__(T) red32_final(const __grid_constant__ Red32Args A) {
+    __shared__ float s0[T], s1[T];
     const int t = threadIdx.x;
     const int64_t nb = A.nblk;
     int64_t G = 1;
-    while (G * kFinal32 < nb) G <<= 1;
+    while (G * T < nb) G <<= 1;
     const int ng = (int)((nb + G - 1) / G);
     if (t < ng) {
         float *q0 = A.part0 + (int64_t)t * G, *q1 = A.part1 + (int64_t)t * G;
@@ -394,7 +395,8 @@ int run32(const float *xh, const float *xl, const float *yh, const float *yl, in
                                 cudaSuccess)
         return TF_ECUDA;
     kern<<<(unsigned)A.nblk, threads, smem, s>>>(A);
-    if (A.nblk > 1) red32_final<PLAIN><<<1, kFinal32, 0, s>>>(A);
+    if (A.nblk > 8 * kThreads32) red32_final<PLAIN, kFinal32><<<1, kFinal32, 0, s>>>(A);
+    else if (A.nblk > 1) red32_final<PLAIN, kThreads32><<<1, kThreads32, 0, s>>>(A);
     return tfh::launch_status();
 }
 
