@@ -498,6 +498,16 @@ int twofold_server_wait(tf_server *s, uint64_t ticket, int32_t timeout_ms, tf_re
 int twofold_server_stats(tf_server *s, tf_server_stats *out);
 int twofold_server_destroy(tf_server *s);
 
+/* Host-side fault injection, for testing what callers of the server see
+ * when a batch fails (no paper counterpart; no device fault is involved):
+ * from this call on, every `every`-th batch the scheduler starts is failed
+ * before any of its copies or launches, as if one of its CUDA calls had
+ * returned an error.  Its requests complete with TF_ECUDA (counted in the
+ * stats' `failed`), its memory is released, and the server goes on with the
+ * following batches.  every = 0 turns injection off; every < 0 (or s NULL)
+ * is TF_EINVAL. */
+int twofold_server_inject_failures(tf_server *s, int32_t every);
+
 #ifdef __cplusplus
 }
 #endif

@@ -141,6 +141,7 @@ SIGNATURES = {
     "twofold_server_wait": ([_P, ctypes.c_uint64, _I32, ctypes.POINTER(tf_request_info)], ctypes.c_int),
     "twofold_server_stats": ([_P, ctypes.POINTER(tf_server_stats)], ctypes.c_int),
     "twofold_server_destroy": ([_P], ctypes.c_int),
+    "twofold_server_inject_failures": ([_P, _I32], ctypes.c_int),
 }
 
 _lib = None

@@ -181,6 +181,8 @@ struct tf_server {
     tf_batch_config cfg{};
     uint64_t next_id = 1;
     tf_server_stats st{};
+    int inject_every = 0;      // twofold_server_inject_failures: fail every n-th started batch
+    int64_t started = 0;       // batches started since injection was set
 
     void run();
     bool admit(Batch &b);
@@ -363,8 +365,10 @@ void tf_server::run() {
             st.peak_bytes = (int64_t)arena.peak();
             Batch *bp = nb.get();
             inflight.push_back(std::move(nb));
+            const bool injected = inject_every > 0 && ++started % inject_every == 0;
             lk.unlock();
             if (cudaEventCreateWithFlags(&bp->ev, cudaEventDisableTiming) != cudaSuccess) bp->status = TF_ECUDA;
+            else if (injected) bp->status = TF_ECUDA;    // an injected failure: nothing of the batch runs
             else start(*bp);
             lk.lock();
             continue;
@@ -482,6 +486,14 @@ extern "C" int twofold_server_stats(tf_server *s, tf_server_stats *out) {
     out->peak_bytes = (int64_t)s->arena.peak();
     out->pending = (int64_t)s->pending.size();
     out->inflight = (int32_t)s->inflight.size();
+    return TF_OK;
+}
+
+extern "C" int twofold_server_inject_failures(tf_server *s, int32_t every) {
+    if (!s || every < 0) return TF_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    s->inject_every = every;
+    s->started = 0;
     return TF_OK;
 }
 

@@ -101,6 +101,12 @@ class Server:
         _check(st, "twofold_server_wait")
         return t.out
 
+    def inject_failures(self, every: int) -> None:
+        """Fail every `every`-th batch the scheduler starts from now on,
+        before any of its work runs (host-side fault injection for tests;
+        0 turns it off).  Its requests complete with TF_ECUDA."""
+        _check(lib().twofold_server_inject_failures(self._h, every), "twofold_server_inject_failures")
+
     def stats(self) -> dict:
         s = tf_server_stats()
         _check(lib().twofold_server_stats(self._h, ctypes.byref(s)), "twofold_server_stats")

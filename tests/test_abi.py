@@ -223,3 +223,4 @@ def test_server_rejects_bad_arguments(L):
     assert L.twofold_server_submit(None, ctypes.byref(r), ctypes.byref(tid)) == T.TF_EINVAL
     assert L.twofold_server_wait(None, 1, 0, None) == T.TF_EINVAL
     assert L.twofold_server_destroy(None) == T.TF_EINVAL
+    assert L.twofold_server_inject_failures(None, 1) == T.TF_EINVAL

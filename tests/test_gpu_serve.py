@@ -192,3 +192,38 @@ def test_wait_timeout_keeps_the_ticket():
     assert_bits(z[0][idx], r0, "z0")
     assert_bits(z[1][idx], r1, "z1")
     assert_flags(z[2][idx], rf, "flags")
+
+
+def test_injected_batch_failures_are_reported_and_the_server_recovers():
+    """Host-side fault injection (no device fault): with every second batch
+    failed before it runs, requests submitted one at a time (one batch each)
+    alternate between TF_ECUDA and the oracle's bits; the failures are
+    counted, their memory comes back, and with injection off every later
+    request completes correctly."""
+    x, y = synth.dot_uniform(65537, seed=21)
+    e0, e1 = O.reduce(x, None, y, None)
+    with Server(mem_cap=16 << 20) as srv:
+        srv.inject_failures(2)
+        outcomes = []
+        for _ in range(6):
+            t = srv.submit_dot(x, y)
+            try:
+                z = srv.wait(t)
+                assert_bits(z[0], [e0], "z0")
+                assert_bits(z[1], [e1], "z1")
+                outcomes.append(T.TF_OK)
+            except T.TwofoldError as err:
+                assert err.status == T.TF_ECUDA
+                outcomes.append(err.status)
+        assert outcomes == [T.TF_OK, T.TF_ECUDA] * 3, outcomes
+        st = srv.stats()
+        assert st["failed"] == 3 and st["completed"] == 3, st
+        srv.inject_failures(0)
+        for _ in range(4):
+            z = srv.wait(srv.submit_dot(x, y))
+            assert_bits(z[0], [e0], "z0 after")
+            assert_bits(z[1], [e1], "z1 after")
+        st = srv.stats()
+        assert st["failed"] == 3 and st["completed"] == 7, st
+    with pytest.raises(T.TwofoldError):
+        Server(mem_cap=1 << 20).inject_failures(-1)
