@@ -97,7 +97,7 @@ typedef enum {
     TF_ENOSPC = -2,        /* workspace too small                                     */
     TF_ECUDA = -3,         /* CUDA launch / runtime error                             */
     TF_ETIMEOUT = -4,      /* a bounded device-side wait gave up                      */
-    TF_EUNSUPPORTED = -5   /* valid request outside this build's limits               */
+    TF_EUNSUPPORTED = -5   /* valid request outside the library's limits             */
 } tf_status;
 
 /* Human-readable text of a status code (static storage). */
