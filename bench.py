@@ -207,6 +207,86 @@ def graph_throughput(call, reps):
     return {"calls_in_graph": reps, "replays": 3, "us_per_call": us, "calls_per_s": 1e6 / us}
 
 
+# ------------------------------------------------------------- pipe rates
+
+PROBES = {"dadd": 0, "dmul": 1, "dfma": 2, "ffma": 3, "imad": 4, "iadd": 5, "lop": 6, "mulhi64": 7, "mufu": 8,
+          "i2f": 9}
+
+
+def probe_rate(stamps, threads, iters, ops_per_iter=128):
+    """Lane operations per SM clock from the probe's per-CTA stamps (rows of
+    SM id, start clock, end clock, digest): per SM, the operations of its
+    CTAs over the span from their first start to their last end; returns the
+    median over SMs, the spread and the number of SMs seen."""
+    st = np.asarray(stamps, np.int64).reshape(-1, 4)
+    rates = []
+    for s in np.unique(st[:, 0]):
+        r = st[st[:, 0] == s]
+        span = int(r[:, 2].max() - r[:, 1].min())
+        if span > 0:
+            rates.append(len(r) * threads * iters * ops_per_iter / span)
+    rates = np.asarray(rates)
+    return {"op_per_clk_sm": float(np.median(rates)), "min": float(rates.min()), "max": float(rates.max()),
+            "sms": int(rates.size)}
+
+
+def measure_pipes(names=tuple(PROBES), target_cycles=4e6, blocks_per_sm=4, threads=256, reps=3):
+    """Issue rate of each probed instruction kind on this GPU (lane ops per
+    SM clock, the best of `reps` launches of ~target_cycles SM clocks; all
+    CTAs resident at once)."""
+    import torch
+    import paper_1401_6235_gb300 as T
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * blocks_per_sm
+    rec = torch.empty(4 * blocks, dtype=torch.int64, device="cuda")
+    out = {}
+    for name in names:
+        op = PROBES[name]
+        T.pipe_probe(op, 4, blocks, threads, rec)                  # calibration launch
+        torch.cuda.synchronize()
+        cal = probe_rate(rec.cpu().numpy(), threads, 4)["op_per_clk_sm"]
+        iters = max(8, int(target_cycles * cal / (blocks_per_sm * threads * T.PROBE_OPS_PER_ITER)))
+        best = None
+        for _ in range(reps):
+            T.pipe_probe(op, iters, blocks, threads, rec)
+            torch.cuda.synchronize()
+            r = probe_rate(rec.cpu().numpy(), threads, iters)
+            if best is None or r["op_per_clk_sm"] > best["op_per_clk_sm"]:
+                best = r
+        best["iters"] = iters
+        out[name] = best
+    return out
+
+
+def workload_fp64_peak(args, rank, world, dist_on):
+    """The issue rates that bound the binary64 kernels, measured on this
+    GPU: binary64 add / multiply / fma, binary32 fma (issue limit), integer
+    multiply-add, add, logic, 64-bit high multiply, reciprocal seed and
+    integer-to-float conversion, each as lane operations per SM clock, and
+    the same times SMs times the sampled SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    measure_pipes(("dadd",), target_cycles=1e6, reps=1)              # warm-up
+    with ClockSampler(args.smi_index) as cs:
+        t0 = time.perf_counter()
+        rates = measure_pipes()
+        wall = time.perf_counter() - t0
+    clk = cs.summary()
+    mhz = clk["sm_mhz"] or 2070.0
+    for r in rates.values():
+        r["gops"] = r["op_per_clk_sm"] * sms * mhz * 1e6 / 1e9
+    return {
+        "metric": "FP64 pipe issue rate (binary64 add, lane ops per SM clock)",
+        "value": rates["dadd"]["op_per_clk_sm"], "unit": "op/clk/SM", "ms_per_step": wall * 1e3 / len(rates),
+        "pipes": rates, "sms": sms,
+        "config": {"workload": "pipe-rate probes: 8 independent register chains per thread, 128 instructions per "
+                               "loop iteration, 4 CTAs x 256 threads per SM, best of 3 launches of ~4e6 SM clocks",
+                   "l2": "registers only (no memory traffic)", "parallelism": f"replicas x{world}"},
+        "e2e": None, "gpu_launches": 10 * 4 + 1, "clocks": clk,
+        "_kernel_ms": 0.0, "_ops": 0, "_bytes": 0, "_units": None, "_sample": None, "_bound": "none",
+    }
+
+
 # --------------------------------------------------------------- workloads
 
 def workload_ew(args, rank, world, dist_on):
@@ -409,7 +489,10 @@ def workload_cond_dots(args, rank, world, dist_on):
     nchunk = 8 if nj % 8 == 0 else 1
     per_c = nj // nchunk
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    wss = [T.workspace(T.lib().twofold_workspace_bytes(T.KIND_DOT, int(offs_a[-1]), per_c, None)) for _ in streams]
+    chunk_elems = max(int(offs_a[(c + 1) * per_c] - offs_a[c * per_c]) for c in range(nchunk))
+    # one workspace per stream (T.workspace would hand both the same cached buffer)
+    wss = [torch.empty(T.lib().twofold_workspace_bytes(T.KIND_DOT, chunk_elems, per_c, None), dtype=torch.uint8,
+                       device="cuda") for _ in streams]
 
     def e2e_step():
         cur = torch.cuda.current_stream()
@@ -433,6 +516,8 @@ def workload_cond_dots(args, rank, world, dist_on):
     e2e_ms = time_steps(e2e_step, e2e_steps, 3, dist_on) / e2e_steps
     torch.cuda.synchronize()
     e2e_same = all(torch.equal(h.view(torch.uint8), r.view(torch.uint8)) for h, r in zip(hres, ref))
+    if not e2e_same:
+        raise RuntimeError("the chunked end-to-end step changed the bits of the batched call")
     per = ms / args.steps
     return {
         "metric": f"batched twofold dots jobs/s ({nj} x 2^16)", "value": nj * world / (per * 1e-3),
@@ -971,7 +1056,7 @@ def cpu_criteria():
 WORKLOADS = {"ew_chain": workload_ew, "dot": workload_dot, "cond_dots": workload_cond_dots,
              "horner": workload_horner, "batch_mix": workload_batch_mix, "serve": workload_serve,
              "ew_chain_f32": workload_ew_f32, "criteria": workload_criteria,
-             "dot_f32": workload_dot_f32, "dot_sharded": workload_dot_sharded}
+             "dot_f32": workload_dot_f32, "dot_sharded": workload_dot_sharded, "fp64_peak": workload_fp64_peak}
 
 
 # -------------------------------------------------------------- reference
@@ -1022,11 +1107,14 @@ def build_line(res, args, world, sms, hbm, src):
     traffic = round(tr[0] * units) if tr and units else None
     clk = res["clocks"]["sm_mhz"] or 2070.0
     peak_fp64 = FP64_OPS_PER_CLK_SM * sms * clk * 1e6 / 1e12
-    achieved = ops / (kms * 1e-3) / 1e12
+    achieved = ops / (kms * 1e-3) / 1e12 if kms > 0 else None
     bound = res.pop("_bound", "alu")
     if ops == 0:                                   # a serving line: no single kernel to place
         achieved = None
-    if bound == "hbm":
+    if bound == "none":                            # a measurement of the peaks themselves
+        res["roofline"] = None
+        achieved = None
+    elif bound == "hbm":
         gbs = nbytes / (kms * 1e-3) / 1e9
         res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                            "traffic": traffic, "traffic_source": tr[1] if traffic else None,
@@ -1043,8 +1131,9 @@ def build_line(res, args, world, sms, hbm, src):
         pipes = PIPES.get(args.workload)
         if pipes:
             res["roofline"]["ncu_pipes"] = dict(pipes[0], source=pipes[1])
-    res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                  "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
+    if kms > 0:
+        res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
     if sample is not None and not args.no_cpu_baseline and world == 1:    # rank 0 at N = 1 only
         res["cpu_baseline"] = sample()
     line = {"metric": res.pop("metric"), "value": res.pop("value"), "unit": res.pop("unit"),

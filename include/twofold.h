@@ -318,7 +318,10 @@ int twofold_combine(const double *z0, const double *z1, int64_t m, tf_out out1, 
  * 2^31 elements at the default leaf of 256), held on every GPU that loads
  * the library until exit; larger requests return TF_EUNSUPPORTED before any
  * launch.  The first call on a device looks up the array's address with
- * cudaGetSymbolAddress (make it before any stream capture).  All calls
+ * cudaGetSymbolAddress (make it before any stream capture) and keeps it for
+ * the rest of the process: it belongs to the device's primary context, so
+ * after cudaDeviceReset, or under a driver context other than the primary
+ * one, this entry point must not be called on that device.  All calls
  * share the array: calls that overlap on the GPU race; calls ordered on one
  * stream do not. */
 int twofold_dot_noalloc(tf_in x, tf_in y, int64_t n, tf_out out1, const tf_params *p, void *stream);
@@ -507,6 +510,42 @@ int twofold_server_destroy(tf_server *s);
  * following batches.  every = 0 turns injection off; every < 0 (or s NULL)
  * is TF_EINVAL. */
 int twofold_server_inject_failures(tf_server *s, int32_t every);
+
+/* ------------------------------------------------------ pipe-rate probes
+ *
+ * Measurement only (no paper counterpart): the binary64 kernels above are
+ * bound by the SM's FP64 pipe and integer pipes, so their roofline is the
+ * rate at which an SM retires each instruction kind.  One launch of
+ * `blocks` CTAs of `threads` threads (a multiple of 32, at most 1024) runs,
+ * per thread, `iters` x 128 instructions of kind `op` over 8 independent
+ * register chains:
+ *   TF_PROBE_DADD / DMUL / DFMA   binary64 add / multiply / fused multiply-add
+ *   TF_PROBE_FFMA                 binary32 fused multiply-add (the FMA pipe;
+ *                                 at full rate it shows the issue limit)
+ *   TF_PROBE_IMAD                 32-bit integer multiply-add
+ *   TF_PROBE_IADD / TF_PROBE_LOP  32-bit integer add / logic (xor)
+ *   TF_PROBE_MULHI64              high half of a 64 x 64-bit product
+ *   TF_PROBE_MUFU                 binary32 reciprocal square-root
+ *                                 approximation (the special-function unit
+ *                                 that seeds the integer division and root)
+ *   TF_PROBE_I2F                  32-bit unsigned to binary32 conversion
+ * CTA b writes rec[4b .. 4b+3] (device int64 array of 4 * blocks, 8-byte
+ * aligned): its SM id, its start and end SM clock (clock64), and a digest
+ * of its chains.  Lane operations per SM clock on SM s = (threads x iters x
+ * 128 x the CTAs that ran on s) / (last end - first start on s).  Size the
+ * grid so that all CTAs are resident at once.  Asynchronous on `stream`;
+ * TF_EINVAL for an unknown op or bad sizes, TF_ECUDA for a launch error. */
+#define TF_PROBE_DADD 0
+#define TF_PROBE_DMUL 1
+#define TF_PROBE_DFMA 2
+#define TF_PROBE_FFMA 3
+#define TF_PROBE_IMAD 4
+#define TF_PROBE_IADD 5
+#define TF_PROBE_LOP 6
+#define TF_PROBE_MULHI64 7
+#define TF_PROBE_MUFU 8
+#define TF_PROBE_I2F 9
+int twofold_pipe_probe(int32_t op, int64_t iters, int32_t blocks, int32_t threads, int64_t *rec, void *stream);
 
 #ifdef __cplusplus
 }

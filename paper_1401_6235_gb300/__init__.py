@@ -142,6 +142,7 @@ SIGNATURES = {
     "twofold_server_stats": ([_P, ctypes.POINTER(tf_server_stats)], ctypes.c_int),
     "twofold_server_destroy": ([_P], ctypes.c_int),
     "twofold_server_inject_failures": ([_P, _I32], ctypes.c_int),
+    "twofold_pipe_probe": ([_I32, _I64, _I32, _I32, _P, _P], ctypes.c_int),
 }
 
 _lib = None
@@ -561,3 +562,21 @@ def plain_horner_batched(coefs, coef_offs, ks, x, x_offs, out=None, ws=None, str
                                       xo.ctypes.data, _dev(out), _dev(ws), ws.numel(), _stream(stream)),
            "plain_horner_batched")
     return out
+
+
+# ------------------------------------------------------------ pipe-rate probes
+
+PROBE_DADD, PROBE_DMUL, PROBE_DFMA, PROBE_FFMA = 0, 1, 2, 3
+PROBE_IMAD, PROBE_IADD, PROBE_LOP, PROBE_MULHI64, PROBE_MUFU, PROBE_I2F = 4, 5, 6, 7, 8, 9
+#: lane instructions per thread per loop iteration of a probe (8 chains x 16 rounds)
+PROBE_OPS_PER_ITER = 128
+
+
+def pipe_probe(op: int, iters: int, blocks: int, threads: int, rec=None, stream=None):
+    """One launch of the pipe-rate probe (measurement only): returns the
+    int64 CUDA tensor of 4 stamps per CTA (SM id, start clock, end clock,
+    digest)."""
+    torch = _torch()
+    rec = torch.empty(4 * blocks, dtype=torch.int64, device="cuda") if rec is None else rec
+    _check(lib().twofold_pipe_probe(op, iters, blocks, threads, _dev(rec), _stream(stream)), "twofold_pipe_probe")
+    return rec

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-fmad=false", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
               "-Xptxas", "-v"]
 SOURCES = ["tf_abi.cu", "tf_ew.cu", "tf_reduce.cu", "tf_reduce32.cu", "tf_horner.cu", "tf_batch.cu", "tf_serve.cu",
-           "tf_jit.cu"]
+           "tf_jit.cu", "tf_probe.cu"]
 # device headers the runtime compiler of tf_jit.cu gets as text (embedded at build time)
 JIT_HEADERS = ["tf_soft.cuh", "tf_device.cuh", "tf_device_f32.cuh"]
 CUDA_LIB = "/usr/local/cuda/lib64"

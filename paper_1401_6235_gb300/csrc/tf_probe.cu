@@ -1,0 +1,121 @@
+// Issue-rate probes of the SM's execution pipes (measurement only; the paper
+// has no counterpart).  The binary64 twofold kernels are bound by the FP64
+// pipe and the integer pipes, not by HBM, so their roofline needs the rate
+// at which one SM retires each kind of instruction.  Each probe runs long
+// unrolled streams of one instruction over 8 independent register chains
+// per thread; every CTA stamps its SM id and its start and end SM clocks
+// (clock64, taken by thread 0 between barriers), and the host turns the
+// stamps into lane operations per SM clock: per SM, the CTAs' operations
+// over the span from the first start to the last end.  The result does not
+// depend on the SM clock frequency.
+#include "tf_host.cuh"
+
+namespace {
+
+constexpr int kChains = 8;     // independent chains per thread
+constexpr int kRepeat = 16;    // chain rounds per loop iteration (loop overhead below 2 %)
+
+__device__ __forceinline__ unsigned smid() {
+    unsigned s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
+
+// One instruction of the probed kind on chain j.  Integer chains mix in a
+// neighbour chain, so that no two steps fold into one instruction.
+template <int OP>
+__device__ __forceinline__ void step(double (&d)[kChains], float (&f)[kChains], uint32_t (&u)[kChains],
+                                     uint64_t (&w)[kChains], int j, double a, double b, float af, float bf,
+                                     uint32_t m) {
+    if constexpr (OP == TF_PROBE_DADD) {
+        asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(d[j]) : "d"(a));
+    } else if constexpr (OP == TF_PROBE_DMUL) {
+        asm volatile("mul.rn.f64 %0, %0, %1;" : "+d"(d[j]) : "d"(a));
+    } else if constexpr (OP == TF_PROBE_DFMA) {
+        asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(d[j]) : "d"(a), "d"(b));
+    } else if constexpr (OP == TF_PROBE_FFMA) {
+        asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(f[j]) : "f"(af), "f"(bf));
+    } else if constexpr (OP == TF_PROBE_IMAD) {
+        asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(u[j]) : "r"(m), "r"(u[(j + 1) & 7]));
+    } else if constexpr (OP == TF_PROBE_IADD) {
+        asm volatile("add.u32 %0, %0, %1;" : "+r"(u[j]) : "r"(u[(j + 1) & 7]));
+    } else if constexpr (OP == TF_PROBE_LOP) {
+        asm volatile("xor.b32 %0, %0, %1;" : "+r"(u[j]) : "r"(u[(j + 3) & 7]));
+    } else if constexpr (OP == TF_PROBE_MULHI64) {   // several instructions per operation
+        asm volatile("mul.hi.u64 %0, %0, %1;" : "+l"(w[j]) : "l"(w[(j + 1) & 7]));
+    } else if constexpr (OP == TF_PROBE_MUFU) {   // a chain of roots (a chain of reciprocals could cancel)
+        asm volatile("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(f[j]));
+    } else {   // TF_PROBE_I2F: the converted bits feed the next conversion of the chain
+        asm volatile("{\n\t.reg .f32 t;\n\tcvt.rn.f32.u32 t, %0;\n\tmov.b32 %0, t;\n\t}" : "+r"(u[j]));
+    }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(1024) pipe_probe_kernel(int64_t iters, double a, double b, uint32_t m,
+                                                          long long *rec) {
+    double d[kChains];
+    float f[kChains];
+    uint32_t u[kChains];
+    uint64_t w[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) {
+        d[j] = 1.0 + 0.125 * j;
+        f[j] = 1.0f + 0.125f * (float)j;
+        u[j] = threadIdx.x * 2654435761u + (uint32_t)j;
+        w[j] = ((uint64_t)u[j] << 32) | 0x9E3779B9u;
+    }
+    const float af = (float)a, bf = (float)b;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < kRepeat; ++r) {
+#pragma unroll
+            for (int j = 0; j < kChains; ++j) step<OP>(d, f, u, w, j, a, b, af, bf, m);
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    // keep every chain live (the stamps' slot 3 receives a digest of them)
+    uint64_t dig = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j)
+        dig ^= (uint64_t)__double_as_longlong(d[j]) ^ __float_as_uint(f[j]) ^ u[j] ^ w[j];
+    if (threadIdx.x == 0) {
+        rec[4 * blockIdx.x + 0] = smid();
+        rec[4 * blockIdx.x + 1] = t0;
+        rec[4 * blockIdx.x + 2] = t1;
+        rec[4 * blockIdx.x + 3] = (long long)dig;
+    }
+}
+
+template <int OP>
+cudaError_t launch(int64_t iters, int blocks, int threads, long long *rec, cudaStream_t s) {
+    pipe_probe_kernel<OP><<<blocks, threads, 0, s>>>(iters, 1.0, 0x1p-60, 0x9E3779B1u, rec);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int twofold_pipe_probe(int32_t op, int64_t iters, int32_t blocks, int32_t threads, int64_t *rec,
+                                  void *stream) {
+    if (iters < 0 || blocks < 1 || threads < 32 || threads > 1024 || threads % 32 != 0) return TF_EINVAL;
+    if (!tfh::dptr_ok(rec)) return TF_EINVAL;
+    long long *r = reinterpret_cast<long long *>(rec);
+    cudaStream_t s = tfh::as_stream(stream);
+    cudaError_t e;
+    switch (op) {
+    case TF_PROBE_DADD: e = launch<TF_PROBE_DADD>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_DMUL: e = launch<TF_PROBE_DMUL>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_DFMA: e = launch<TF_PROBE_DFMA>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_FFMA: e = launch<TF_PROBE_FFMA>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_IMAD: e = launch<TF_PROBE_IMAD>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_IADD: e = launch<TF_PROBE_IADD>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_LOP: e = launch<TF_PROBE_LOP>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_MULHI64: e = launch<TF_PROBE_MULHI64>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_MUFU: e = launch<TF_PROBE_MUFU>(iters, blocks, threads, r, s); break;
+    case TF_PROBE_I2F: e = launch<TF_PROBE_I2F>(iters, blocks, threads, r, s); break;
+    default: return TF_EINVAL;
+    }
+    return e == cudaSuccess ? TF_OK : TF_ECUDA;
+}

@@ -736,7 +736,11 @@ extern "C" int plain_dot_batched(const double *x, const double *y, const int64_t
 // array of this library, reserved on every GPU that loads it until the
 // process exits.  The array's address comes from cudaGetSymbolAddress, once
 // per device, on the first call made with that device current; make that
-// first call before any stream capture.  All calls share the one array, so
+// first call before any stream capture.  The address is kept per device
+// index for the life of the process, so it is the one of the primary
+// context: a program that resets the device (cudaDeviceReset) or works
+// under another driver context must not call this entry point on that
+// device afterwards.  All calls share the one array, so
 // calls whose kernels overlap on the GPU (different streams, no ordering)
 // race; calls ordered on one stream do not.  Nothing here needs zeroing:
 // every partial is written before it is read.

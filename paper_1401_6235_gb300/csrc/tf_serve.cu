@@ -340,7 +340,7 @@ void tf_server::run() {
             }
             if (e != cudaSuccess) (void)cudaGetLastError();
             finish(b, b.status != TF_OK ? b.status : (e == cudaSuccess ? TF_OK : TF_ECUDA));
-            cudaEventDestroy(b.ev);
+            if (b.ev) cudaEventDestroy(b.ev);        // null when its creation failed
             inflight.erase(inflight.begin() + (long)i);
         }
         if (stop && pending.empty() && inflight.empty()) break;

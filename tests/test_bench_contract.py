@@ -59,3 +59,29 @@ def test_reference_arm_prints_its_line():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_peak_measurement_line_has_no_roofline():
+    """The pipe-rate workload measures the peaks themselves: its line keeps
+    the contract's keys with a null roofline and no HBM block."""
+    res = fake("alu")
+    res.update({"_kernel_ms": 0.0, "_ops": 0, "_bytes": 0, "_units": None, "_sample": None, "_bound": "none",
+                "e2e": None})
+    args = types.SimpleNamespace(workload="fp64_peak", steps=3, warmup=3, no_cpu_baseline=False)
+    line = bench.build_line(res, args, 1, 152, 6784.5, "measured")
+    assert KEYS <= set(line) and line["roofline"] is None and "hbm" not in line
+    json.dumps(line)
+
+
+def test_probe_rate_from_stamps():
+    """Lane operations per SM clock from per-CTA stamps: per SM, the CTAs'
+    operations over the first start to the last end; median over SMs."""
+    import numpy as np
+    threads, iters = 256, 10
+    ops = threads * iters * 128
+    st = np.array([[0, 100, 100 + ops // 2, 0], [0, 150, 100 + ops, 0],       # SM 0: 2 CTAs over `ops` clocks
+                   [3, 0, ops, 0],                                              # SM 3: 1 CTA over `ops` clocks
+                   [5, 10, 10 + ops // 4, 0]], np.int64)                        # SM 5: 1 CTA over ops/4 clocks
+    r = bench.probe_rate(st, threads, iters)
+    assert r["sms"] == 3 and r["min"] == pytest.approx(1.0) and r["max"] == pytest.approx(4.0)
+    assert r["op_per_clk_sm"] == pytest.approx(2.0)
