@@ -38,11 +38,24 @@ sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-# FP64 issue rate of one GB300 SM: the nominal 1.25 TFLOP/s FP64 of the part is
-# 2 DFMA per clock per SM on 152 SMs at 2.07 GHz (2 FLOP each); a stream of
-# independent add, mul or fma measures 1.6 op/clk/SM.  The FP64 roofline below
-# is 2 op/clk/SM times SMs times the SM clock sampled during the timed region.
-FP64_OPS_PER_CLK_SM = 2.0
+# The binary64 kernels are bound by the SM's execution pipes, not by HBM.
+# Their roofline: per pipe, the lane-instruction slots a unit of work takes
+# on that pipe (warp instructions executed on it x 32 / units, from one ncu
+# capture of the kernel, named beside) over the pipe's rate, which bench.py
+# measures live with the pipe-rate probes (lane ops per SM clock, the probe
+# named in PIPE_PROBE) times SMs times the sampled SM clock.  The pipe with
+# the largest floor is the bound; frac = that floor / the measured time.
+# "issue" counts every issued instruction against the issue limit (the FP32
+# fma probe, which runs at the issue rate).
+PIPE_PROBE = {"fp64": "dadd", "alu": "shf", "fmaheavy": "imad", "issue": "ffma"}
+PIPE_LOAD = {
+    "ew_chain": ({"fp64": 17.00, "alu": 707.00, "fmaheavy": 340.67, "issue": 1243.45}, "element",
+                 "profiles/tf_jit_ew_chain_n2e28.md"),
+    "horner": ({"fp64": 4.000, "alu": 130.40, "fmaheavy": 45.46, "issue": 203.53}, "point step",
+               "profiles/horner_kernel_k5-30_2e24.md"),
+    "cond_dots": ({"fp64": 3.064, "alu": 150.06, "fmaheavy": 45.02, "issue": 220.08}, "element",
+                  "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
+}
 
 # Algorithmic unit costs (bytes and basic FP64 operations per result).
 EW_BYTES = 8 * 8 + 2 * 8 + 1            # 4 twofold inputs, twofold output, flag byte
@@ -61,25 +74,20 @@ HORNER_OPS_PER_STEP = 4 + 7              # MTF1.1 + ATF1.1
 # profiles/), scaled by the units a launch processes; None where the kernel
 # changed after its counters were taken.
 TRAFFIC_PER_UNIT = {
-    "ew_chain": ((281.741e6 + 85.110e6) * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
+    "ew_chain": (370.68e6 * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
     "ew_chain_f32": ((536.904e6 + 130.459e6) * 16 / (1 << 28), "profiles/tf_jit_ew_chain_f32_n2e28.md"),
-    "horner": ((268.576e6 + 515.401e6) * 2 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
-    "cond_dots": ((268.51e6 + 3.47e6) / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
+    "horner": (783.06e6 * 2 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
+    "cond_dots": (271.71e6 / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
     "dot": (1.120256e6 / 65536, "profiles/reduce_lat_dot_n65536.md"),
     "dot_f32": ((536.895e6 + 3.582e6) / (1 << 26), "profiles/red32_blocks_dot_f32_2e28.md"),
 }
 
-# ncu pipe activity of the dominant kernel (fraction of its peak sustained
-# rate: FP64 pipe, integer ALU pipe, instruction issue) from the committed
-# profiles: the binary64 kernels run part of their arithmetic on the integer
-# pipes, so the alu roofline's frac (algorithmic FP64 operations against the
-# FP64 pipe alone) can exceed 1 while neither pipe is full.
-PIPES = {
-    "ew_chain": ({"fp64": 0.745, "alu": 0.719, "issue": 0.632}, "profiles/tf_jit_ew_chain_n2e28.md"),
-    "horner": ({"fp64": 0.808, "alu": 0.774, "issue": 0.591}, "profiles/horner_kernel_k5-30_2e24.md"),
-    "cond_dots": ({"fp64": 0.290, "alu": 0.444, "issue": 0.330}, "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
-    "dot": ({"fp64": 0.252, "alu": 0.081}, "profiles/reduce_lat_dot_n65536.md"),
-}
+# FP64 instructions per unit that the paper's algorithms themselves need
+# (the chain: MTF1 3 add + 3 mul, ATF1 3 add, DTF1 2 add + 1 fma, RTF1 5 add;
+# a Horner step: MTF1.1 1 mul + 1 add, ATF1.1 2 add; a dotted dot element:
+# ATF1 3 add, the Two-Product on the integer pipes), the rest of their
+# arithmetic running on the integer pipes with the same bits.
+ALG_FP64 = {"ew_chain": 17, "horner": 4, "cond_dots": 3, "dot": 3}
 
 
 def measured_peaks():
@@ -209,8 +217,7 @@ def graph_throughput(call, reps):
 
 # ------------------------------------------------------------- pipe rates
 
-PROBES = {"dadd": 0, "dmul": 1, "dfma": 2, "ffma": 3, "imad": 4, "iadd": 5, "lop": 6, "mulhi64": 7, "mufu": 8,
-          "i2f": 9}
+PROBES = {"dadd": 0, "dmul": 1, "dfma": 2, "ffma": 3, "imad": 4, "shf": 5, "mulhi64": 6, "mufu": 7, "i2f": 8}
 
 
 def probe_rate(stamps, threads, iters, ops_per_iter=128):
@@ -258,12 +265,35 @@ def measure_pipes(names=tuple(PROBES), target_cycles=4e6, blocks_per_sm=4, threa
     return out
 
 
+def measure_latencies(names=("dadd", "dmul", "dfma", "imad"), target_cycles=1e6):
+    """Dependent-chain latency in SM clocks: one warp per SM runs one chain
+    per thread (32 lanes over the measured lane rate)."""
+    import torch
+    import paper_1401_6235_gb300 as T
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    rec = torch.empty(4 * sms, dtype=torch.int64, device="cuda")
+    out = {}
+    for name in names:
+        op = PROBES[name] | T.PROBE_LATENCY
+        T.pipe_probe(op, 2, sms, 32, rec)
+        torch.cuda.synchronize()
+        cal = probe_rate(rec.cpu().numpy(), 32, 2)["op_per_clk_sm"]
+        iters = max(4, int(target_cycles * cal / (32 * T.PROBE_OPS_PER_ITER)))
+        T.pipe_probe(op, iters, sms, 32, rec)
+        torch.cuda.synchronize()
+        r = probe_rate(rec.cpu().numpy(), 32, iters)
+        out[name] = {"cycles": 32.0 / r["op_per_clk_sm"], "iters": iters}
+    return out
+
+
 def workload_fp64_peak(args, rank, world, dist_on):
     """The issue rates that bound the binary64 kernels, measured on this
     GPU: binary64 add / multiply / fma, binary32 fma (issue limit), integer
-    multiply-add, add, logic, 64-bit high multiply, reciprocal seed and
-    integer-to-float conversion, each as lane operations per SM clock, and
-    the same times SMs times the sampled SM clock."""
+    multiply-add, funnel shift (integer ALU), 64-bit high multiply, root
+    seed and integer-to-float conversion, each as lane operations per SM
+    clock, and the same times SMs times the sampled SM clock; and the
+    dependent-chain latency of binary64 add / multiply / fma and integer
+    multiply-add in SM clocks."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     measure_pipes(("dadd",), target_cycles=1e6, reps=1)              # warm-up
@@ -271,6 +301,7 @@ def workload_fp64_peak(args, rank, world, dist_on):
         t0 = time.perf_counter()
         rates = measure_pipes()
         wall = time.perf_counter() - t0
+        lat = measure_latencies()
     clk = cs.summary()
     mhz = clk["sm_mhz"] or 2070.0
     for r in rates.values():
@@ -278,11 +309,11 @@ def workload_fp64_peak(args, rank, world, dist_on):
     return {
         "metric": "FP64 pipe issue rate (binary64 add, lane ops per SM clock)",
         "value": rates["dadd"]["op_per_clk_sm"], "unit": "op/clk/SM", "ms_per_step": wall * 1e3 / len(rates),
-        "pipes": rates, "sms": sms,
+        "pipes": rates, "latency_cycles": lat, "sms": sms,
         "config": {"workload": "pipe-rate probes: 8 independent register chains per thread, 128 instructions per "
                                "loop iteration, 4 CTAs x 256 threads per SM, best of 3 launches of ~4e6 SM clocks",
                    "l2": "registers only (no memory traffic)", "parallelism": f"replicas x{world}"},
-        "e2e": None, "gpu_launches": 10 * 4 + 1, "clocks": clk,
+        "e2e": None, "gpu_launches": len(PROBES) * 4 + 1, "clocks": clk,
         "_kernel_ms": 0.0, "_ops": 0, "_bytes": 0, "_units": None, "_sample": None, "_bound": "none",
     }
 
@@ -433,7 +464,7 @@ def workload_dot(args, rank, world, dist_on):
         "graph": graph,
         "latency_floor": dot_latency_floor(cs.summary().get("sm_mhz"), per * 1e3),
         "gpu_launches": 2 * args.steps, "clocks": cs.summary(),    # leaves kernel + final tree
-        "_kernel_ms": per, "_ops": DOT_OPS * n, "_bytes": DOT_BYTES * n, "_units": n,
+        "_kernel_ms": per, "_ops": DOT_OPS * n, "_bytes": DOT_BYTES * n, "_units": n, "_bound": "latency",
         "_sample": lambda: cpu_sample_dot(n),
     }
 
@@ -594,7 +625,7 @@ def workload_horner(args, rank, world, dist_on):
                    "n": int(x.size), "l2": "inputs 512 MiB larger than L2", "parallelism": f"replicas x{world}"},
         "gpu_launches": args.steps, "clocks": cs.summary(),
         "_kernel_ms": per, "_ops": HORNER_OPS_PER_STEP * steps_total + len(ks) * npts,
-        "_bytes": HORNER_BYTES * x.size, "_units": x.size, "_sample": None,
+        "_bytes": HORNER_BYTES * x.size, "_units": x.size, "_pipe_units": steps_total, "_sample": None,
     }
 
 
@@ -692,8 +723,9 @@ def workload_serve(args, rank, world, dist_on):
     import synth
     rng = np.random.default_rng(2000 + rank)
     nreq = args.n or 100000
-    rates = [2000.0, 4000.0, 8000.0, 16000.0]
-    per_rate = [min(nreq, int(8 * r)) for r in rates[:-1]] + [nreq]    # ~8 s of arrivals below the top rate
+    rates = getattr(args, "serve_rates", None) or [2000.0, 4000.0, 8000.0, 16000.0]
+    secs = getattr(args, "serve_seconds", None) or 8.0
+    per_rate = [min(nreq, int(secs * r)) for r in rates[:-1]] + [nreq]    # ~secs of arrivals below the top rate
     pool = 1 << 24
     pin = lambda m: torch.empty(m, dtype=torch.float64).pin_memory().numpy()
     xy = synth.ew_chain(pool, seed=rank, pinned=pin)              # 8 pinned pools of 2^24 doubles
@@ -1094,43 +1126,69 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------- line
 
-def build_line(res, args, world, sms, hbm, src):
+def pipe_roofline(wl, pipe_units, kms, rates, sms, mhz):
+    """Per-pipe floors of the dominant kernel (PIPE_LOAD x units over the
+    measured pipe rates at the sampled clock) and the roofline of the
+    binding pipe; None where the kernel has no committed counts."""
+    load = PIPE_LOAD.get(wl)
+    if not load or not rates or not pipe_units or kms <= 0:
+        return None
+    per, unit_of_work, src = load
+    hz = sms * mhz * 1e6
+    floors = {p: slots * pipe_units / (rates[PIPE_PROBE[p]] * hz) * 1e3 for p, slots in per.items()
+              if rates.get(PIPE_PROBE[p])}
+    bound = max(floors, key=floors.get)
+    achieved = per[bound] * pipe_units / (kms * 1e-3) / 1e12
+    peak = rates[PIPE_PROBE[bound]] * hz / 1e12
+    r = {"bound": "alu", "pipe": bound, "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+         "frac": achieved / peak, "floors_ms": floors, "kernel_ms": kms,
+         "load_per_unit": per, "unit_of_work": unit_of_work, "load_source": src,
+         "pipe_rates": {p: rates[PIPE_PROBE[p]] for p in per if rates.get(PIPE_PROBE[p])},
+         "what": "lane instructions of the binding pipe per second (ncu count per unit x units / kernel time) vs "
+                 "its rate measured in this run by the pipe-rate probes (lane ops per SM clock x SMs x sampled "
+                 "clock); frac = the pipe's floor / the kernel time"}
+    alg = ALG_FP64.get(wl)
+    if alg and rates.get("dadd"):
+        fp64_peak = rates["dadd"] * hz / 1e12
+        a = alg * pipe_units / (kms * 1e-3) / 1e12
+        r["fp64_algorithmic"] = {"per_unit": alg, "achieved": a, "peak": fp64_peak, "frac": a / fp64_peak,
+                                 "what": "FP64 instructions the paper's algorithms need per unit, per second, vs "
+                                         "the measured FP64 rate"}
+    return r
+
+
+def build_line(res, args, world, sms, hbm, src, rates=None):
     """The JSON line of a workload's result dict: the contract's keys, the
-    roofline of the dominant kernel (alu: the algorithms' basic FP64 ops
-    against the FP64 issue rate at the sampled clock; hbm: algorithmic bytes
-    against the measured copy bandwidth) and the CPU baseline sample."""
+    roofline of the dominant kernel (alu: its binding execution pipe, per
+    pipe_roofline; hbm: algorithmic bytes against the measured copy
+    bandwidth) and the CPU baseline sample."""
     res = dict(res)
     sample = res.pop("_sample")
     kms, ops, nbytes = res.pop("_kernel_ms"), res.pop("_ops"), res.pop("_bytes")
     units = res.pop("_units", None)
+    pipe_units = res.pop("_pipe_units", units)
     tr = TRAFFIC_PER_UNIT.get(args.workload)
     traffic = round(tr[0] * units) if tr and units else None
     clk = res["clocks"]["sm_mhz"] or 2070.0
-    peak_fp64 = FP64_OPS_PER_CLK_SM * sms * clk * 1e6 / 1e12
-    achieved = ops / (kms * 1e-3) / 1e12 if kms > 0 else None
     bound = res.pop("_bound", "alu")
-    if ops == 0:                                   # a serving line: no single kernel to place
-        achieved = None
-    if bound == "none":                            # a measurement of the peaks themselves
+    if bound == "none" or kms <= 0:                # a measurement of the peaks themselves
         res["roofline"] = None
-        achieved = None
+    elif bound == "latency":                       # one short reduction: its dependent chain bounds it
+        f = res["latency_floor"]
+        res["roofline"] = {"bound": "latency", "pipe": "fp64 dependent adds", "achieved": f["floor_us"] / f["frac"],
+                           "floor": f["floor_us"], "unit": "us", "frac": f["frac"], "traffic": traffic,
+                           "traffic_source": tr[1] if traffic else None, "what": f["what"]}
     elif bound == "hbm":
         gbs = nbytes / (kms * 1e-3) / 1e9
         res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                            "traffic": traffic, "traffic_source": tr[1] if traffic else None,
                            "what": f"algorithmic bytes per launch / launch time vs the {src} copy bandwidth"}
-        achieved = None
-    elif achieved is None:
-        res["roofline"] = None
-    if achieved is not None:
-        res["roofline"] = {
-            "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp64, "traffic": traffic, "traffic_source": tr[1] if traffic else None,
-            "what": "basic FP64 ops of the algorithms (div, sqrt = 1) per second vs the FP64 "
-                    f"pipe issue rate ({FP64_OPS_PER_CLK_SM} op/clk/SM x {sms} SMs x sampled clock)"}
-        pipes = PIPES.get(args.workload)
-        if pipes:
-            res["roofline"]["ncu_pipes"] = dict(pipes[0], source=pipes[1])
+    else:
+        r = pipe_roofline(args.workload, pipe_units, kms, rates, sms, clk) if ops else None
+        if r is not None:
+            r["traffic"] = traffic
+            r["traffic_source"] = tr[1] if traffic else None
+        res["roofline"] = r
     if kms > 0:
         res["hbm"] = {"achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": nbytes / (kms * 1e-3) / 1e9 / hbm, "peak_source": src}
@@ -1144,6 +1202,44 @@ def build_line(res, args, world, sms, hbm, src):
     return line
 
 
+# ------------------------------------------------------------ sub-results
+
+SUB_KEEP = ("metric", "value", "unit", "ms_per_step", "plain_ms_per_step", "slowdown_vs_plain",
+            "plain_int_ms_per_step", "slowdown_vs_plain_int", "graph", "latency_floor", "persistent_batch",
+            "per_job_launches", "speedup_vs_per_job", "same_bits_as_per_job", "tuned_config", "sweep", "e2e",
+            "clocks", "gbs")
+
+
+def subresult(name, fn, args, over, rank, world, dist_on, sms, hbm, src, rates):
+    """One other workload of the hot path, shortened, for the default line:
+    its headline figures and its roofline, built as its own line would be."""
+    import types
+    a = types.SimpleNamespace(**vars(args))
+    a.workload = name
+    for k, v in over.items():
+        setattr(a, k, v)
+    a.no_cpu_baseline = True
+    t0 = time.perf_counter()
+    res = fn(a, rank, world, dist_on)
+    line = build_line(res, a, world, sms, hbm, src, rates)
+    out = {k: line[k] for k in SUB_KEEP if k in line}
+    out.update({"steps": a.steps, "config": line["config"], "roofline": line.get("roofline"),
+                "hbm_frac": (line.get("hbm") or {}).get("frac"), "wall_s": time.perf_counter() - t0})
+    return out
+
+
+# The other measured rows, run after the chain in the default line: the
+# 65536-element dot, the 4096 ill-conditioned dots, the batched Horner, the
+# mixed persistent batch and a shortened serving sweep.
+SUBRESULTS = [
+    ("dot", {"steps": 200, "warmup": 20, "n": 0}),
+    ("cond_dots", {"steps": 10, "warmup": 3, "n": 0}),
+    ("horner", {"steps": 10, "warmup": 3, "n": 0}),
+    ("batch_mix", {"steps": 10, "warmup": 3, "n": 0}),
+    ("serve", {"steps": 1, "warmup": 3, "n": 10000, "serve_rates": [2000.0, 8000.0], "serve_seconds": 2.0}),
+]
+
+
 # ------------------------------------------------------------------- main
 
 def main():
@@ -1155,6 +1251,8 @@ def main():
     ap.add_argument("--workload", default="ew_chain", choices=sorted(WORKLOADS))
     ap.add_argument("--n", type=int, default=0, help="override the problem size (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-subresults", action="store_true",
+                    help="default workload only: skip the other rows' shortened runs")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -1178,11 +1276,25 @@ def main():
     import paper_1401_6235_gb300 as T
     entry.build() if not os.path.exists(T.LIB_PATH) else None
 
+    # the pipe rates of this GPU, for the roofline of pipe-bound kernels
+    rates = None
+    if args.workload in PIPE_LOAD:
+        m = measure_pipes(tuple(sorted(set(PIPE_PROBE.values()))), target_cycles=2e6, reps=2)
+        rates = {k: v["op_per_clk_sm"] for k, v in m.items()}
     res = WORKLOADS[args.workload](args, rank, world, dist_on)
+    hbm, src = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    subs = {}
+    if args.workload == "ew_chain" and not args.no_subresults and not args.n:
+        m = measure_pipes(tuple(sorted(set(PIPE_PROBE.values()))), target_cycles=2e6, reps=2)
+        r2 = {k: v["op_per_clk_sm"] for k, v in m.items()}
+        for name, over in SUBRESULTS:
+            subs[name] = subresult(name, WORKLOADS[name], args, over, rank, world, dist_on, sms, hbm, src, r2)
+            torch.cuda.empty_cache()
     if rank == 0:
-        hbm, src = measured_peaks()
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        line = build_line(res, args, world, sms, hbm, src)
+        line = build_line(res, args, world, sms, hbm, src, rates)
+        if subs:
+            line["subresults"] = subs
         print(json.dumps(line), flush=True)
     if dist_on:
         import torch.distributed as dist

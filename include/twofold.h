@@ -523,12 +523,15 @@ int twofold_server_inject_failures(tf_server *s, int32_t every);
  *   TF_PROBE_FFMA                 binary32 fused multiply-add (the FMA pipe;
  *                                 at full rate it shows the issue limit)
  *   TF_PROBE_IMAD                 32-bit integer multiply-add
- *   TF_PROBE_IADD / TF_PROBE_LOP  32-bit integer add / logic (xor)
+ *   TF_PROBE_SHF                  32-bit funnel shift (the integer ALU pipe)
  *   TF_PROBE_MULHI64              high half of a 64 x 64-bit product
  *   TF_PROBE_MUFU                 binary32 reciprocal square-root
  *                                 approximation (the special-function unit
  *                                 that seeds the integer division and root)
  *   TF_PROBE_I2F                  32-bit unsigned to binary32 conversion
+ * op | TF_PROBE_LATENCY (DADD, DMUL, DFMA, IMAD only) runs the same count as
+ * one dependent chain per thread: with one warp per SM, 32 / (lane ops per
+ * SM clock) is the latency of one instruction in SM clocks.
  * CTA b writes rec[4b .. 4b+3] (device int64 array of 4 * blocks, 8-byte
  * aligned): its SM id, its start and end SM clock (clock64), and a digest
  * of its chains.  Lane operations per SM clock on SM s = (threads x iters x
@@ -540,11 +543,11 @@ int twofold_server_inject_failures(tf_server *s, int32_t every);
 #define TF_PROBE_DFMA 2
 #define TF_PROBE_FFMA 3
 #define TF_PROBE_IMAD 4
-#define TF_PROBE_IADD 5
-#define TF_PROBE_LOP 6
-#define TF_PROBE_MULHI64 7
-#define TF_PROBE_MUFU 8
-#define TF_PROBE_I2F 9
+#define TF_PROBE_SHF 5
+#define TF_PROBE_MULHI64 6
+#define TF_PROBE_MUFU 7
+#define TF_PROBE_I2F 8
+#define TF_PROBE_LATENCY 0x100
 int twofold_pipe_probe(int32_t op, int64_t iters, int32_t blocks, int32_t threads, int64_t *rec, void *stream);
 
 #ifdef __cplusplus

@@ -19,8 +19,9 @@ namespace tf {
 struct d2 { double z0, z1; };
 
 // ------------------------------------------------------------------ bits
-__device__ __forceinline__ uint64_t bits_of(double v) { return (uint64_t)__double_as_longlong(v); }
-__device__ __forceinline__ double from_bits(uint64_t b) { return __longlong_as_double((long long)b); }
+// (opaque moves, see soft::d2u: sign work on the bits stays on the integer pipes)
+__device__ __forceinline__ uint64_t bits_of(double v) { return soft::d2u(v); }
+__device__ __forceinline__ double from_bits(uint64_t b) { return soft::u2d(b); }
 __device__ __forceinline__ bool finite_bits(double v) {
     return ((bits_of(v) >> 52) & 0x7FF) != 0x7FF;
 }
@@ -177,17 +178,22 @@ __device__ __forceinline__ d2 rpf11(double x0) {
 // RTF1: z0 = sqrt(x0); (u0,u1) = Two-Sum(x0, x1); (v0,v1) = RPF1(u0,u1);
 //       (w0,w1) = STF1.1((v0,v1), z0); z1 = w0 + w1.
 // The root of u0 (a few ulps from x0) starts from the reciprocal root that
-// the root of x0 produced (soft::sqrt_rn_near; same correctly rounded bits).
+// the root of x0 produced (soft::sqrt_rn_near; same correctly rounded bits),
+// and RPF1's division by 2 v0 reuses that estimate.  v0 and z0 are roots of
+// nearby values, so STF1.1's difference v0 - z0 is usually exact and its
+// tail +0 without the general Two-Diff tail (soft::diff_err_near_bits).
 __device__ __forceinline__ d2 rtf1(double x0, double x1) {
     uint64_t yz;
     const double z0 = soft::sqrt_rn_y(x0, &yz);
     double u0, u1;
     two_sum(x0, x1, u0, u1);
     double d;                                                // fma(-v0, v0, u0), packed
-    const double v0 = soft::sqrt_rn_near(u0, x0, yz, &d);   // RPF1 on (u0, u1)
-    const double v1 = soft::div_rn(__dadd_rn(u1, d), twice(v0));
-    const d2 w = stf11(v0, v1, z0);
-    return {z0, __dadd_rn(w.z0, w.z1)};
+    uint64_t yv;
+    const double v0 = soft::sqrt_rn_near(u0, x0, yz, &d, &yv);   // RPF1 on (u0, u1)
+    const double v1 = soft::div_rn_y(__dadd_rn(u1, d), twice(v0), yv);
+    const double w0 = __dsub_rn(v0, z0);                     // STF1.1((v0, v1), z0)
+    const double w1 = __dadd_rn(v1, from_bits(soft::diff_err_near_bits(bits_of(v0), bits_of(z0), bits_of(w0))));
+    return {z0, __dadd_rn(w0, w1)};
 }
 
 // -------------------------------------------- coupled (Dekker emulation)
@@ -323,7 +329,7 @@ struct FlagCfg {
 // ulp(v) = 2^(max(e,-1022)-52) from the exponent field; NaN for Inf/NaN.
 __device__ __forceinline__ double ulp_of(double v) {
     int e = (int)((bits_of(v) >> 52) & 0x7FF);
-    if (e == 0x7FF) return __longlong_as_double(0x7FF8000000000000LL);
+    if (e == 0x7FF) return from_bits(0x7FF8000000000000ull);
     if (e == 0) e = 1;
     int p = e - 1075;                       // exponent of the ulp, >= -1074
     if (p >= -1022) return from_bits((uint64_t)(p + 1023) << 52);

@@ -7,7 +7,9 @@
 // (clock64, taken by thread 0 between barriers), and the host turns the
 // stamps into lane operations per SM clock: per SM, the CTAs' operations
 // over the span from the first start to the last end.  The result does not
-// depend on the SM clock frequency.
+// depend on the SM clock frequency.  The latency form runs the same number
+// of instructions as ONE dependent chain per thread: with one warp per SM,
+// 32 lanes over the measured rate is the latency of one instruction.
 #include "tf_host.cuh"
 
 namespace {
@@ -22,7 +24,9 @@ __device__ __forceinline__ unsigned smid() {
 }
 
 // One instruction of the probed kind on chain j.  Integer chains mix in a
-// neighbour chain, so that no two steps fold into one instruction.
+// neighbour chain, so that no two steps fold into one instruction (chains
+// of associative integer adds or logic ops are not used: the compiler
+// merges them into three-input instructions).
 template <int OP>
 __device__ __forceinline__ void step(double (&d)[kChains], float (&f)[kChains], uint32_t (&u)[kChains],
                                      uint64_t (&w)[kChains], int j, double a, double b, float af, float bf,
@@ -37,10 +41,8 @@ __device__ __forceinline__ void step(double (&d)[kChains], float (&f)[kChains], 
         asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(f[j]) : "f"(af), "f"(bf));
     } else if constexpr (OP == TF_PROBE_IMAD) {
         asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(u[j]) : "r"(m), "r"(u[(j + 1) & 7]));
-    } else if constexpr (OP == TF_PROBE_IADD) {
-        asm volatile("add.u32 %0, %0, %1;" : "+r"(u[j]) : "r"(u[(j + 1) & 7]));
-    } else if constexpr (OP == TF_PROBE_LOP) {
-        asm volatile("xor.b32 %0, %0, %1;" : "+r"(u[j]) : "r"(u[(j + 3) & 7]));
+    } else if constexpr (OP == TF_PROBE_SHF) {   // a funnel shift does not merge with its neighbours
+        asm volatile("shf.l.wrap.b32 %0, %0, %1, 13;" : "+r"(u[j]) : "r"(u[(j + 1) & 7]));
     } else if constexpr (OP == TF_PROBE_MULHI64) {   // several instructions per operation
         asm volatile("mul.hi.u64 %0, %0, %1;" : "+l"(w[j]) : "l"(w[(j + 1) & 7]));
     } else if constexpr (OP == TF_PROBE_MUFU) {   // a chain of roots (a chain of reciprocals could cancel)
@@ -50,7 +52,7 @@ __device__ __forceinline__ void step(double (&d)[kChains], float (&f)[kChains], 
     }
 }
 
-template <int OP>
+template <int OP, bool LAT>
 __global__ void __launch_bounds__(1024) pipe_probe_kernel(int64_t iters, double a, double b, uint32_t m,
                                                           long long *rec) {
     double d[kChains];
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(1024) pipe_probe_kernel(int64_t iters, double 
 #pragma unroll
         for (int r = 0; r < kRepeat; ++r) {
 #pragma unroll
-            for (int j = 0; j < kChains; ++j) step<OP>(d, f, u, w, j, a, b, af, bf, m);
+            for (int j = 0; j < kChains; ++j) step<OP>(d, f, u, w, LAT ? 0 : j, a, b, af, bf, m);
         }
     }
     __syncthreads();
@@ -90,8 +92,9 @@ __global__ void __launch_bounds__(1024) pipe_probe_kernel(int64_t iters, double 
 }
 
 template <int OP>
-cudaError_t launch(int64_t iters, int blocks, int threads, long long *rec, cudaStream_t s) {
-    pipe_probe_kernel<OP><<<blocks, threads, 0, s>>>(iters, 1.0, 0x1p-60, 0x9E3779B1u, rec);
+cudaError_t launch(bool lat, int64_t iters, int blocks, int threads, long long *rec, cudaStream_t s) {
+    if (lat) pipe_probe_kernel<OP, true><<<blocks, threads, 0, s>>>(iters, 1.0, 0x1p-60, 0x9E3779B1u, rec);
+    else pipe_probe_kernel<OP, false><<<blocks, threads, 0, s>>>(iters, 1.0, 0x1p-60, 0x9E3779B1u, rec);
     return cudaGetLastError();
 }
 
@@ -103,18 +106,21 @@ extern "C" int twofold_pipe_probe(int32_t op, int64_t iters, int32_t blocks, int
     if (!tfh::dptr_ok(rec)) return TF_EINVAL;
     long long *r = reinterpret_cast<long long *>(rec);
     cudaStream_t s = tfh::as_stream(stream);
+    const bool lat = (op & TF_PROBE_LATENCY) != 0;
+    if (lat && op != (TF_PROBE_LATENCY | TF_PROBE_DADD) && op != (TF_PROBE_LATENCY | TF_PROBE_DMUL) &&
+        op != (TF_PROBE_LATENCY | TF_PROBE_DFMA) && op != (TF_PROBE_LATENCY | TF_PROBE_IMAD))
+        return TF_EINVAL;
     cudaError_t e;
-    switch (op) {
-    case TF_PROBE_DADD: e = launch<TF_PROBE_DADD>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_DMUL: e = launch<TF_PROBE_DMUL>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_DFMA: e = launch<TF_PROBE_DFMA>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_FFMA: e = launch<TF_PROBE_FFMA>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_IMAD: e = launch<TF_PROBE_IMAD>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_IADD: e = launch<TF_PROBE_IADD>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_LOP: e = launch<TF_PROBE_LOP>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_MULHI64: e = launch<TF_PROBE_MULHI64>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_MUFU: e = launch<TF_PROBE_MUFU>(iters, blocks, threads, r, s); break;
-    case TF_PROBE_I2F: e = launch<TF_PROBE_I2F>(iters, blocks, threads, r, s); break;
+    switch (op & ~TF_PROBE_LATENCY) {
+    case TF_PROBE_DADD: e = launch<TF_PROBE_DADD>(lat, iters, blocks, threads, r, s); break;
+    case TF_PROBE_DMUL: e = launch<TF_PROBE_DMUL>(lat, iters, blocks, threads, r, s); break;
+    case TF_PROBE_DFMA: e = launch<TF_PROBE_DFMA>(lat, iters, blocks, threads, r, s); break;
+    case TF_PROBE_FFMA: e = launch<TF_PROBE_FFMA>(lat, iters, blocks, threads, r, s); break;
+    case TF_PROBE_IMAD: e = launch<TF_PROBE_IMAD>(lat, iters, blocks, threads, r, s); break;
+    case TF_PROBE_SHF: e = launch<TF_PROBE_SHF>(lat, iters, blocks, threads, r, s); break;
+    case TF_PROBE_MULHI64: e = launch<TF_PROBE_MULHI64>(lat, iters, blocks, threads, r, s); break;
+    case TF_PROBE_MUFU: e = launch<TF_PROBE_MUFU>(lat, iters, blocks, threads, r, s); break;
+    case TF_PROBE_I2F: e = launch<TF_PROBE_I2F>(lat, iters, blocks, threads, r, s); break;
     default: return TF_EINVAL;
     }
     return e == cudaSuccess ? TF_OK : TF_ECUDA;

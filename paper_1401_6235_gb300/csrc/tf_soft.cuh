@@ -46,9 +46,16 @@ constexpr uint64_t kFrac = 0x000FFFFFFFFFFFFFull;
 constexpr uint64_t kHid = 0x0010000000000000ull;
 constexpr uint64_t kSign = 0x8000000000000000ull;
 
+// Bit moves between binary64 and integer registers.  On the device they are
+// opaque register moves (inline PTX), so that the compiler does not turn a
+// sign-bit mask or flip on the bits into a floating-point absolute value or
+// negation, which it would issue on the FP64 pipe (one FP64 instruction
+// each); with the moves opaque, sign work stays on the integer pipes.
 TFS_HD uint64_t d2u(double x) {
 #if defined(__CUDA_ARCH__)
-    return (uint64_t)__double_as_longlong(x);
+    uint64_t u;
+    asm("mov.b64 %0, %1;" : "=l"(u) : "d"(x));
+    return u;
 #else
     uint64_t u;
     std::memcpy(&u, &x, 8);
@@ -58,7 +65,9 @@ TFS_HD uint64_t d2u(double x) {
 
 TFS_HD double u2d(uint64_t u) {
 #if defined(__CUDA_ARCH__)
-    return __longlong_as_double((long long)u);
+    double x;
+    asm("mov.b64 %0, %1;" : "=d"(x) : "l"(u));
+    return x;
 #else
     double x;
     std::memcpy(&x, &u, 8);
@@ -550,10 +559,11 @@ TFS_HD double add_rn(double a, double b) {
 // v, the bits of fma(-v, v, u) (Algorithm 5's exact residual).
 // The general case of sqrt_rn_near (u far from x, or a special value):
 // the full root, and its residual where rem is wanted.
-TFS_COLD double sqrt_near_general(double u, double *rem) {
+TFS_COLD double sqrt_near_general(double u, double *rem, uint64_t *y_out) {
     const uint64_t uu = d2u(u);
     uint64_t y;
     const double v = sqrt_rn_y(u, &y);
+    if (y_out) *y_out = y;
     if (rem) {
         // fma(-v, v, u) without a native operation where the root is NaN
         // (NaN), +Inf (-Inf + Inf: NaN) or a zero (v = u, -u u + u = u)
@@ -565,19 +575,29 @@ TFS_COLD double sqrt_near_general(double u, double *rem) {
     return v;
 }
 
-TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx, double *rem = nullptr) {
+// With y_out != nullptr, *y_out receives a reciprocal estimate for dividing
+// by 2 v (the divisor RTF1's RPF1 step takes) that div_rn_y accepts: on the
+// near path, yx lowered by 2^-44 relative (v and sqrt(x) share the binade
+// and differ by at most 2^-45 relative, and yx is within 2^-52 of the
+// reciprocal of sqrt(x)'s significand, so the lowered value is never above
+// the reciprocal of v's significand and at most 1.5 2^-44 below it); on the
+// general path, the full root's own estimate; 0 (no estimate) for a NaN root.
+TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx, double *rem = nullptr, uint64_t *y_out = nullptr) {
     const uint64_t uu = d2u(u), ux = d2u(x);
     // a negative radicand or a NaN with the sign bit set: NaN root and
     // residual, resolved here because they are common (a chain whose value
     // went negative) while the general case below is rare
     if ((uu >> 63) && (uu << 1)) {
         if (rem) *rem = u2d(0x7FF8000000000000ull);
+        if (y_out) *y_out = 0;
         return u2d(0x7FF8000000000000ull);
     }
     const int f = (int)(uu >> 52);
     const uint64_t mu = (uu & kFrac) | kHid, mx = (ux & kFrac) | kHid;
     const uint64_t diff = mu > mx ? mu - mx : mx - mu;
-    if (yx == 0 || f != (int)(ux >> 52) || (unsigned)(f - 1) >= 2046u || diff > 256) return sqrt_near_general(u, rem);
+    if (yx == 0 || f != (int)(ux >> 52) || (unsigned)(f - 1) >= 2046u || diff > 256)
+        return sqrt_near_general(u, rem, y_out);
+    if (y_out) *y_out = yx - (yx >> 44);
     const int odd = f & 1;
     const int s = odd ? 52 : 53;
     const uint64_t m_hi = mu >> (64 - s), m_lo = mu << s;
@@ -707,6 +727,16 @@ TFS_HD uint64_t sum_err_bits(uint64_t ua, uint64_t ub, uint64_t us) {
         return sign | ((uint64_t)(lead + 1023) << 52) | frac;
     }
     return sign | (mag << (qmin + 1074));               // subnormal tail
+}
+
+// The tail of Algorithm 2.2 (Two-Diff) of a - b, d = RN(a - b), for
+// operands that are usually close: when a and b are finite with the same
+// sign and the same exponent field, b/2 <= a <= 2b (or both are subnormal),
+// so a - b is exact (Sterbenz) and every step of the sequence is exact: the
+// tail is +0.  Otherwise the general tail (sum_err_bits of a, -b, d).
+TFS_HD uint64_t diff_err_near_bits(uint64_t ua, uint64_t ub, uint64_t ud) {
+    if (((ua ^ ub) >> 52) == 0 && ((ua >> 52) & 0x7FF) != 0x7FF) return 0;
+    return sum_err_bits(ua, ub ^ kSign, ud);
 }
 
 }  // namespace soft

@@ -366,4 +366,66 @@ int64_t check_remainder_specials(uint64_t key, int64_t n, double *bad) {
     return nbad;
 }
 
+// RPF1's division by 2 v inside RTF1: v = sqrt(u) for u within a few hundred
+// ulps of x (binade edges included, some far enough for the full root),
+// divided with the reciprocal estimate sqrt_rn_near hands out, against the
+// CPU's t / (2 sqrt(u)).
+int64_t check_div_by_near_root(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double x = std::fabs(rnd(key, 2 * i, 1, 2046));
+        int64_t k = (int64_t)(mix(key ^ (uint64_t)i) % 1200) - 600;
+        if (i % 11 == 0) x = u2d((d2u(x) & ~kFrac) | (i & 1 ? 0 : kFrac));
+        double u = u2d(d2u(x) + k);
+        if (!(u > 0) || std::isinf(u)) continue;
+        double t = rnd(key, 2 * i + 1, 1, 2046);
+        if (i % 3 == 0) t = std::ldexp(t, -(int)(i % 60));
+        uint64_t yx, yv;
+        (void)sqrt_rn_y(x, &yx);
+        double d;
+        const double v = sqrt_rn_near(u, x, yx, &d, &yv);
+        const double got = div_rn_y(t, twice(v), yv);
+        volatile double vr = std::sqrt(u);
+        volatile double w = 2.0 * vr;
+        volatile double ref = t / w;
+        if (!same(v, vr) || !same(got, ref)) {
+            if (!nbad) { bad[0] = t; bad[1] = u; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
+// The Two-Diff tail with the Sterbenz short cut against the literal
+// sequence: pairs in one binade (the short cut), neighbours across a binade
+// edge, random pairs, and a fixed list of special values (zeros of both
+// signs, subnormals, Inf, NaN, the largest finite values).
+int64_t check_diff_err_near(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    const double inf = INFINITY, big = 1.7976931348623157e308;
+    const double vals[] = {0.0, -0.0, inf, -inf, NAN, 1.0, -1.0, 1.5, big, -big, 4.9406564584124654e-324,
+                           -1e-310, 1e-310, 2.2250738585072014e-308, 2.0, 0.75};
+    const int nv = (int)(sizeof(vals) / sizeof(vals[0]));
+    for (int64_t i = 0; i < n + nv * nv; ++i) {
+        double a, b;
+        if (i >= n) {
+            a = vals[(i - n) / nv];
+            b = vals[(i - n) % nv];
+        } else {
+            a = rnd(key, 2 * i, 1, 2046);
+            if (i % 3 == 0) b = u2d(d2u(a) + (int64_t)(mix(key + i) % 2000) - 1000);      // one binade, mostly
+            else if (i % 3 == 1) b = u2d((d2u(a) & ~kFrac) - (i & 2 ? 1 : 0));             // a binade edge
+            else b = rnd(key, 2 * i + 1, 1, 2046);
+        }
+        volatile double d = a - b;
+        const double ref = literal_two_diff_tail(a, b);
+        const double got = u2d(diff_err_near_bits(d2u(a), d2u(b), d2u(d)));
+        if (!same(got, ref)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 }  // extern "C"

@@ -30,20 +30,30 @@ def fake(bound):
     return res
 
 
+RATES = {"dadd": 1.7, "shf": 64.0, "imad": 64.0, "ffma": 128.0}
+
+
 @pytest.mark.parametrize("bound", ["alu", "hbm"])
 def test_line_has_the_contract_keys(bound):
     args = types.SimpleNamespace(workload="ew_chain", steps=3, warmup=3, no_cpu_baseline=False)
-    line = bench.build_line(fake(bound), args, 1, 152, 6784.5, "measured")
+    line = bench.build_line(fake(bound), args, 1, 152, 6784.5, "measured", RATES)
     assert KEYS <= set(line), KEYS - set(line)
     assert "cpu_baseline" in line and line["cpu_baseline"]["kind"] == "oracle"
     r = line["roofline"]
     assert r["bound"] == bound and set(r) >= {"achieved", "peak", "unit", "frac", "traffic"}
     if bound == "alu":
-        assert r["peak"] == pytest.approx(2.0 * 152 * 2000.0 * 1e6 / 1e12)
-        assert r["achieved"] == pytest.approx(8e9 / 4e-3 / 1e12)
-        # the chain kernel's pipe activity, named with the profile it comes from
-        p = r["ncu_pipes"]
-        assert 0 < p["fp64"] <= 1 and 0 < p["alu"] <= 1 and os.path.exists(os.path.join(ROOT, p["source"]))
+        # the binding pipe: the largest floor of the chain kernel's committed per-element counts
+        per, _, src = bench.PIPE_LOAD["ew_chain"]
+        assert os.path.exists(os.path.join(ROOT, src))
+        units, hz = 1 << 28, 152 * 2000.0 * 1e6
+        floors = {p: per[p] * units / (RATES[bench.PIPE_PROBE[p]] * hz) * 1e3 for p in per}
+        assert r["pipe"] == max(floors, key=floors.get)
+        assert r["floors_ms"] == pytest.approx(floors)
+        assert r["peak"] == pytest.approx(RATES[bench.PIPE_PROBE[r["pipe"]]] * hz / 1e12)
+        assert r["achieved"] == pytest.approx(per[r["pipe"]] * units / 4e-3 / 1e12)
+        assert r["frac"] == pytest.approx(max(floors.values()) / 4.0)
+        a = r["fp64_algorithmic"]
+        assert a["frac"] == pytest.approx(bench.ALG_FP64["ew_chain"] * units / 4e-3 / (1.7 * hz))
     else:
         assert r["achieved"] == pytest.approx(4e9 / 4e-3 / 1e9) and r["peak"] == 6784.5
         assert line["dtype"] == "f32"

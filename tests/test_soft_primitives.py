@@ -24,7 +24,8 @@ def H(tmp_path_factory):
         getattr(L, name).argtypes = [u64, i64, ctypes.c_int, ctypes.c_int, p]
         getattr(L, name).restype = i64
     for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared",
-                 "check_sqrt_near", "check_scale_pow2", "check_remainder_specials"):
+                 "check_sqrt_near", "check_scale_pow2", "check_remainder_specials", "check_div_by_near_root",
+                 "check_diff_err_near"):
         getattr(L, name).argtypes = [u64, i64, p]
         getattr(L, name).restype = i64
     L.soft_div.argtypes = [d, d]
@@ -83,6 +84,11 @@ def test_diff_err_matches_literal_two_diff(H):
     run(H, "check_diff_err", 15, 1_000_000, 1980, 2046)
 
 
+def test_sterbenz_diff_tail_matches_literal_two_diff(H):
+    """RTF1's Two-Diff tail with the exact-difference short cut."""
+    run(H, "check_diff_err_near", 32, 2_000_000)
+
+
 @pytest.mark.parametrize("scale", SCALES)
 def test_div_with_reused_reciprocals(H, scale):
     H.set_seed_scale(scale)
@@ -90,6 +96,7 @@ def test_div_with_reused_reciprocals(H, scale):
         run(H, "check_div_by_root", 19, 2_000_000)
         run(H, "check_div_shared", 20, 2_000_000)
         run(H, "check_sqrt_near", 29, 2_000_000)
+        run(H, "check_div_by_near_root", 31, 2_000_000)
     finally:
         H.set_seed_scale(1.0)
 
