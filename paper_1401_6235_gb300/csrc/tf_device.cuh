@@ -159,19 +159,22 @@ __device__ __forceinline__ d2 dtf1(double x0, double x1, double y0, double y1) {
     return {q, soft::div_rn_y(c0, d0, yd)};
 }
 
+// The residual fma(-z0, z0, x0) of Algorithm 5 comes packed from the integer
+// root's own exact remainder (soft::sqrt_rn_y, same bits).
+
 // RPF1: z0 = sqrt(x0); z1 = (x1 + fma(-z0, z0, x0)) / (2 z0).
 __device__ __forceinline__ d2 rpf1(double x0, double x1) {
     uint64_t y;
-    const double c = soft::sqrt_rn_y(x0, &y);
-    const double d = __fma_rn(-c, c, x0);
+    double d;
+    const double c = soft::sqrt_rn_y(x0, &y, &d);
     return {c, soft::div_rn_y(__dadd_rn(x1, d), twice(c), y)};
 }
 
 // RPF1.1: z0 = sqrt(x0); z1 = fma(-z0, z0, x0) / (2 z0).
 __device__ __forceinline__ d2 rpf11(double x0) {
     uint64_t y;
-    const double c = soft::sqrt_rn_y(x0, &y);
-    const double d = __fma_rn(-c, c, x0);
+    double d;
+    const double c = soft::sqrt_rn_y(x0, &y, &d);
     return {c, soft::div_rn_y(d, twice(c), y)};
 }
 
@@ -182,6 +185,9 @@ __device__ __forceinline__ d2 rpf11(double x0) {
 // and RPF1's division by 2 v0 reuses that estimate.  v0 and z0 are roots of
 // nearby values, so STF1.1's difference v0 - z0 is usually exact and its
 // tail +0 without the general Two-Diff tail (soft::diff_err_near_bits).
+// (A short cut for u0 = x0 that reused z0's root and residual measured
+// slower on the chain workload: enough lanes of a warp have tails that move
+// the head for the warp to run both paths.)
 __device__ __forceinline__ d2 rtf1(double x0, double x1) {
     uint64_t yz;
     const double z0 = soft::sqrt_rn_y(x0, &yz);

@@ -91,6 +91,19 @@ TFS_HD int clz64(uint64_t v) {
 #endif
 }
 
+// (x y) >> 64 from the three largest 32 x 32-bit products (the low one
+// dropped): at most 1 below the exact value.  Cheaper than the full high
+// product where a routine's error budget absorbs the unit.
+TFS_HD uint64_t mulhi3(uint64_t x, uint64_t y) {
+    const uint64_t x1 = x >> 32, x0 = x & 0xFFFFFFFFull, y1 = y >> 32, y0 = y & 0xFFFFFFFFull;
+    const uint64_t m1 = x1 * y0, m2 = x0 * y1;
+    return x1 * y1 + (m1 >> 32) + (m2 >> 32) + (((m1 & 0xFFFFFFFFull) + (m2 & 0xFFFFFFFFull)) >> 32);
+}
+
+// (x y) >> 64 from the high words alone, below the exact value by less than
+// 2^33: for quotient corrections whose scale makes that a fraction of a unit.
+TFS_HD uint64_t mulhi1(uint64_t x, uint64_t y) { return (x >> 32) * (y >> 32); }
+
 // Seed tests may perturb on the host: relative factor applied to seeds.
 #if !defined(__CUDA_ARCH__)
 inline float &host_seed_scale() {
@@ -226,22 +239,6 @@ TFS_HD uint64_t recip1(uint64_t mb) {
     return ovf ? ~0ull : y;
 }
 
-// Y ~ 2^116 / mb for a 53-bit significand mb in [2^52, 2^53), i.e. 1/d in
-// 1.63 fixed point with d = mb / 2^53 in [1/2, 1); relative error < 2^-60.
-TFS_HD uint64_t recip_fixed(uint64_t mb) {
-    // seed: rcp of the top 24 bits, 2^29/mb = 2^-24/d -> Y0 = r * 2^87
-    uint64_t y = float_fixed(rcp_seed((float)(uint32_t)(mb >> 29)), 63);
-    const uint64_t dt = mb << 11;                       // d * 2^64
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const uint64_t t = mulhi(dt, y);                // d w 2^63, close to 2^63
-        const uint64_t e = 0 - t;                       // (2 - d w) 2^63, as 2^64 - t
-        const uint64_t lo = y * e, hi = mulhi(y, e);    // y e = w (2 - d w) 2^126
-        y = (hi >> 63) ? ~0ull : (hi << 1) | (lo >> 63);
-    }
-    return y;
-}
-
 // The significand of b in [2^52, 2^53) (meaningful for normal b only).
 TFS_HD uint64_t signif(double b) { return (d2u(b) & kFrac) | kHid; }
 
@@ -317,10 +314,14 @@ TFS_HD double div_rn_y(double a, double b, uint64_t y_in, double *rem) {
     // 2^-43 below, so the estimate is at most 3 units above and 2^10 below
     // Q: q - 4 is below Q and the remainder N - q mb lies in [mb, 2^63.01),
     // exact modulo 2^64.
-    uint64_t q = (mulhi(ma << 11, y) >> (11 - sh)) - 4;
+    // (mulhi3 is at most one unit low before the shift: the estimate stays
+    // within those bounds up to one more unit below, and the remainder
+    // below 2^63.01)
+    uint64_t q = (mulhi3(ma << 11, y) >> (11 - sh)) - 4;
     uint64_t r = (ma << (52 + sh)) - q * mb;
-    // one correction step dq ~ r / mb = r y / 2^116, off by at most one
-    const uint64_t dq = mulhi(r, y) >> 52;
+    // one correction step dq ~ r / mb = r y / 2^116, off by at most one (the
+    // high-word product is low by under 2^33, 2^-19 units of dq)
+    const uint64_t dq = mulhi1(r, y) >> 52;
     q += dq;
     r -= dq * mb;
     if ((int64_t)r < 0) { q -= 1; r += mb; }
@@ -345,23 +346,34 @@ TFS_HD double div_rn_y(double a, double b, uint64_t y_in, double *rem) {
 // Correctly rounded sqrt(a); *y_out receives 1/sqrt(m) as w 2^63 (m the
 // normalised radicand significand), which estimates 2^116 / signif(sqrt(a))
 // within 2^-52 relative (0 when the special-value path was taken).
-TFS_HD double sqrt_rn_y(double a, uint64_t *y_out);
+// With rem != nullptr, *rem also receives RN(a - c^2) for the returned root
+// c, the bits of fma(-c, c, a) (Algorithm 5's exact residual).
+TFS_HD double sqrt_rn_y(double a, uint64_t *y_out, double *rem = nullptr);
 
 TFS_HD double sqrt_rn(double a) {
     uint64_t y;
     return sqrt_rn_y(a, &y);
 }
 
-TFS_HD double sqrt_rn_y(double a, uint64_t *y_out) {
+TFS_HD double sqrt_rn_y(double a, uint64_t *y_out, double *rem) {
     *y_out = 0;
     const uint64_t u = d2u(a);
     const int f = (int)(u >> 52);                        // sign and exponent field
     if ((unsigned)(f - 1) >= 2046u) {
-        // IEEE special cases in integer form; positive subnormals go native
-        if ((u << 1) == 0) return a;                           // sqrt(+-0) = +-0
-        if (u >> 63) return u2d(0x7FF8000000000000ull);        // negative or -NaN
-        if (f == 0x7FF) return a;                              // +Inf, +NaN
-        return native_sqrt(a);
+        // IEEE special cases in integer form; positive subnormals go native.
+        // Residuals: a for a zero (-0 * 0 + 0 keeps the zero's sign), NaN
+        // for a negative radicand, Inf (-Inf + Inf) or NaN.
+        if ((u << 1) == 0) {                                   // sqrt(+-0) = +-0
+            if (rem) *rem = a;
+            return a;
+        }
+        if ((u >> 63) || f == 0x7FF) {
+            if (rem) *rem = u2d(0x7FF8000000000000ull);
+            return (u >> 63) ? u2d(0x7FF8000000000000ull) : a;   // negative or -NaN; +Inf, +NaN
+        }
+        const double c = native_sqrt(a);
+        if (rem) *rem = native_fma(u2d(d2u(c) ^ kSign), c, a);
+        return c;
     }
     const uint64_t mx = (u & kFrac) | kHid;
     const int odd = f & 1;                               // unbiased exponent even
@@ -371,26 +383,45 @@ TFS_HD double sqrt_rn_y(double a, uint64_t *y_out) {
     const uint64_t mt = (m_hi << 22) | (m_lo >> 42);     // m 2^64, m = M / 2^106 in [1/4, 1)
     // w = 1/sqrt(m) in (1, 2] as Y = w 2^63; seed rsqrt(mt / 2^40) = w 2^-12
     uint64_t y = float_fixed(rsqrt_seed((float)(uint32_t)(mt >> 40)), 75);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const uint64_t w2 = mulhi(y, y);                 // w^2 2^62
-        const uint64_t t = mulhi(mt, w2);                // m w^2 2^62, close to 2^62
+    // Newton steps w' = w (3 - m w^2)/2 (never above 1/sqrt(m)).  The first
+    // starts from the 24-bit seed and runs on high words only (each product
+    // low by under 2^-29 relative), which leaves w within ~2^-28; the second
+    // takes three-word products (low by at most one unit) and lands within
+    // ~2^-56 below 1/sqrt(m).
+    {
+        const uint64_t w2 = mulhi1(y, y);                // w^2 2^62
+        const uint64_t t = mulhi1(mt, w2);               // m w^2 2^62, close to 2^62
         const uint64_t e = 0xC000000000000000ull - t;    // (3 - m w^2) 2^62, close to 2^63
-        const uint64_t lo = y * e, hi = mulhi(y, e);     // w (3 - m w^2) 2^125
-        y = (hi >> 63) ? ~0ull : (hi << 1) | (lo >> 63); // w' 2^63, w' = w (3 - m w^2)/2
+        const uint64_t hi = mulhi1(y, e);                // w (3 - m w^2) 2^125 / 2^64
+        y = (hi >> 63) ? ~0ull : (hi << 1);              // w' 2^63
+    }
+    {
+        const uint64_t w2 = mulhi3(y, y);
+        const uint64_t t = mulhi3(mt, w2);
+        const uint64_t e = 0xC000000000000000ull - t;
+        const uint64_t hi = mulhi3(y, e);
+        y = (hi >> 63) ? ~0ull : (hi << 1);
     }
     *y_out = y;
     // sqrt(M) = m w 2^53 ~ mulhi(mt, y) / 2^10
-    uint64_t q = mulhi(mt, y) >> 10;
+    uint64_t q = mulhi3(mt, y) >> 10;
     int64_t r = (int64_t)(m_lo - q * q);                 // M - q^2, exact: |r| < 2^60
     if (r < 0) { q -= 1; r += (int64_t)(2 * q + 1); }
     if (r < 0) { q -= 1; r += (int64_t)(2 * q + 1); }
     if (r > (int64_t)(2 * q)) { r -= (int64_t)(2 * q + 1); q += 1; }
     if (r > (int64_t)(2 * q)) { r -= (int64_t)(2 * q + 1); q += 1; }
     // round to nearest: up iff M > (q + 1/2)^2, i.e. r > q (no ties exist)
-    q += (uint64_t)(r > (int64_t)q);
+    const bool up = r > (int64_t)q;
     const int fr = (f + 1022 + odd) >> 1;                // biased exponent of the root
-    return u2d(((uint64_t)(fr - 1) << 52) + q);
+    const double c = u2d(((uint64_t)(fr - 1) << 52) + q + (uint64_t)up);
+    if (rem) {
+        // a - c^2 = (M - Q^2) 2^(2 er - 104), Q the returned significand
+        const int64_t rs = up ? r - (int64_t)(2 * q + 1) : r;
+        uint64_t rb;
+        if (pack_exact(rs, 2 * (fr - 1023) - 104, &rb)) *rem = u2d(rb);
+        else *rem = native_fma(u2d(d2u(c) ^ kSign), c, a);
+    }
+    return c;
 }
 
 // 2 * c exactly as the IEEE multiplication, in integer form: an exponent
@@ -418,6 +449,17 @@ TFS_HD double native_mul(double a, double b) {
 #endif
 }
 
+// The exact 106-bit product P = ma mb of two significands below 2^53 as
+// (hi, lo) 64-bit words, from four 32 x 32-bit products: the high halves
+// are below 2^21, so every partial sum stays below 2^64.
+TFS_HD void mul53(uint64_t ma, uint64_t mb, uint64_t &hi, uint64_t &lo) {
+    const uint64_t a0 = ma & 0xFFFFFFFFull, a1 = ma >> 32, b0 = mb & 0xFFFFFFFFull, b1 = mb >> 32;
+    const uint64_t p00 = a0 * b0;
+    const uint64_t mid = a0 * b1 + a1 * b0 + (p00 >> 32);   // < 2^54 + 2^32
+    lo = (mid << 32) | (p00 & 0xFFFFFFFFull);
+    hi = a1 * b1 + (mid >> 32);
+}
+
 // Correctly rounded a * b.  Normal operands whose product is normal (or
 // overflows) run on the integer pipes: the 106-bit product of the
 // significands, one normalisation step, round to nearest even on the
@@ -439,13 +481,13 @@ TFS_HD double mul_rn(double a, double b) {
         if (e > 2046 && fa != 0 && fb != 0) return u2d(sign | inf);   // product >= 2^1024
         return native_mul(a, b);
     }
-    const uint64_t ma = ((ua & kFrac) | kHid) << 11, mb = ((ub & kFrac) | kHid) << 11;
-    const uint64_t hi = mulhi(ma, mb), lo = ma * mb;     // product of significands << 22
-    const int top = (int)(hi >> 63);                     // product in [2, 4)
-    const int gb = 10 + top;                             // guard bits below the 53-bit significand
-    uint64_t q = hi >> gb;
-    const uint64_t rem = hi & ((1ull << gb) - 1), half = 1ull << (gb - 1);
-    q += (rem > half) | ((rem == half) & ((lo != 0) | (q & 1)));
+    uint64_t hi, lo;
+    mul53((ua & kFrac) | kHid, (ub & kFrac) | kHid, hi, lo);   // P in [2^104, 2^106)
+    const int top = (int)(hi >> 41);                     // product of significands in [2, 4)
+    const int sh = 52 + top;                             // bits below the 53-bit significand
+    uint64_t q = (hi << (12 - top)) | (lo >> sh);
+    const uint64_t R = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    q += (R > half) | ((R == half) & ((q & 1) != 0));
     const uint64_t r = ((uint64_t)(e + top - 1) << 52) + q, inf = 0x7FF0000000000000ull;
     return u2d(sign | (r >= inf ? inf : r));            // past the top binade: Inf
 }
@@ -478,21 +520,24 @@ TFS_HD void two_prod_rn(double a, double b, double &p, double &e) {
         return;
     }
     const uint64_t ma = (ua & kFrac) | kHid, mb = (ub & kFrac) | kHid;
-    const uint64_t hi = mulhi(ma << 11, mb << 11), lo = (ma << 11) * (mb << 11);   // P 2^22
-    const int top = (int)(hi >> 63);                     // P in [2^105, 2^106)
-    const int gb = 10 + top;
-    uint64_t q = hi >> gb;
-    const uint64_t rem = hi & ((1ull << gb) - 1), half = 1ull << (gb - 1);
-    q += (rem > half) | ((rem == half) & ((lo != 0) | (q & 1)));
+    uint64_t hi, lo;
+    mul53(ma, mb, hi, lo);                               // P in [2^104, 2^106), hi in [2^40, 2^42)
+    const int top = (int)(hi >> 41);                     // P >= 2^105
+    const int sh = 52 + top;                             // bits below the 53-bit significand
+    uint64_t q = (hi << (12 - top)) | (lo >> sh);       // P >> sh, in [2^52, 2^53)
+    const uint64_t R = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    const bool up = (R > half) | ((R == half) & ((q & 1) != 0));
+    q += up;
     p = u2d(sign | (((uint64_t)(ef + top - 1) << 52) + q));
-    // e = P - q 2^(52+top) in units of 2^(ef-1127); |e| <= 2^(51+top): exact mod 2^64
-    const int64_t ei = (int64_t)(ma * mb - (q << (52 + top)));
+    // e = P - q 2^sh in units of 2^(ef-1127): R, or R - 2^sh after rounding
+    // up; |e| <= 2^(sh-1)
+    const int64_t ei = up ? (int64_t)R - (int64_t)(1ull << sh) : (int64_t)R;
     if (ei == 0) { e = 0.0; return; }
     const uint64_t se = sign ^ (ei < 0 ? kSign : 0);
     const uint64_t mag = (uint64_t)(ei < 0 ? -ei : ei);
-    const int lz = clz64(mag);
+    const int lz = clz64(mag);                           // >= 11: mag < 2^53
     const int lead = 63 - lz + ef - 1127;                // exponent of e's leading bit, >= -1016
-    e = u2d(se | ((uint64_t)(lead + 1023) << 52) | (((mag << lz) >> 11) & kFrac));
+    e = u2d(se | ((uint64_t)(lead + 1023) << 52) | ((mag << (lz - 11)) & kFrac));
 }
 
 // Correctly rounded a + b.  Normal operands run on the integer pipes: the
@@ -604,10 +649,11 @@ TFS_HD double sqrt_rn_near(double u, double x, uint64_t yx, double *rem = nullpt
     const uint64_t mt = (m_hi << 22) | (m_lo >> 42);
     // the estimate is within 257 units of Q; 260 below it, the remainder
     // M - q^2 lies in [0, 2^63.02) and is exact modulo 2^64
-    uint64_t q = (mulhi(mt, yx) >> 10) - 260;
+    uint64_t q = (mulhi3(mt, yx) >> 10) - 260;
     uint64_t r = m_lo - q * q;
-    // dq ~ r / (2 q) = r w / 2^54 / ... = mulhi(r, yx) / 2^53
-    const uint64_t dq = mulhi(r, yx) >> 53;
+    // dq ~ r / (2 q) = r w / 2^54 / ... = mulhi(r, yx) / 2^53 (high words: low
+    // by under 2^-20 units)
+    const uint64_t dq = mulhi1(r, yx) >> 53;
     q += dq;
     int64_t rr = (int64_t)(m_lo - q * q);                 // |M - q^2| < 2^60 now
     if (rr < 0) { q -= 1; rr += (int64_t)(2 * q + 1); }

@@ -206,6 +206,10 @@ int64_t check_mul(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
     int64_t nbad = 0;
     for (int64_t i = 0; i < n; ++i) {
         double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
+        if (i % 11 == 5 && elo > 300 && ehi < 1700) {   // ties to even (see check_two_prod)
+            a = u2d(0x3FF0000000000001ull + 2 * (mix(key + i) % (1ull << 50)));
+            b = std::ldexp(1.5, (int)(i % 60) - 30);
+        }
         volatile double ref = a * b;
         if (!same(mul_rn(a, b), ref)) {
             if (!nbad) { bad[0] = a; bad[1] = b; }
@@ -278,6 +282,10 @@ int64_t check_two_prod(uint64_t key, int64_t n, int elo, int ehi, double *bad) {
         double a = rnd(key, 2 * i, elo, ehi), b = rnd(key, 2 * i + 1, elo, ehi);
         if (i % 9 == 0) b = std::ldexp(1.0, (int)(i % 40) - 20);        // exact products
         if (i % 13 == 0) a = 0.0;
+        if (i % 11 == 5) {   // ties: an odd significand below 4/3 times 1.5: the low half is exactly 2^51
+            a = u2d(0x3FF0000000000001ull + 2 * (mix(key + i) % (1ull << 50)));
+            b = std::ldexp(1.5, (int)(i % 60) - 30) * (i & 1 ? -1.0 : 1.0);
+        }
         volatile double pr = a * b;
         volatile double er = std::fma(a, b, -pr);
         double p, e;
@@ -301,7 +309,14 @@ int64_t check_remainders(uint64_t key, int64_t n, int elo, int ehi, double *bad)
         volatile double rr = std::fma(-qr, b, a);
         double x = std::fabs(a);
         uint64_t y;
-        (void)sqrt_rn_y(x, &y);
+        double dx;
+        const double cx = sqrt_rn_y(x, &y, &dx);
+        volatile double cxr = std::sqrt(x);
+        volatile double dxr = std::fma(-cxr, cxr, x);
+        if (!same(cx, cxr) || !same(dx, dxr)) {
+            if (!nbad) { bad[0] = x; bad[1] = 0.0; }
+            ++nbad;
+        }
         double u = u2d(d2u(x) + (int64_t)(i % 401) - 200);
         double d;
         double v = sqrt_rn_near(u, x, y, &d);
@@ -357,7 +372,10 @@ int64_t check_remainder_specials(uint64_t key, int64_t n, double *bad) {
             const double v = sqrt_rn_near(a, b, y, &d);
             volatile double vr = std::sqrt(a);
             volatile double dr = std::fma(-vr, vr, a);
-            if (!same(q, qr) || !same(r, rr) || !same(v, vr) || !same(d, dr)) {
+            uint64_t ya;
+            double da;
+            const double va = sqrt_rn_y(a, &ya, &da);
+            if (!same(q, qr) || !same(r, rr) || !same(v, vr) || !same(d, dr) || !same(va, vr) || !same(da, dr)) {
                 if (!nbad) { bad[0] = a; bad[1] = b; }
                 ++nbad;
             }
