@@ -456,6 +456,262 @@ int lat_group(int64_t L, int64_t M) {
 
 size_t lat_smem(int B, int64_t L) { return LatRows(L).bytes(B); }
 
+// ----------------------------------------------------------------------
+// Latency schedule on a CTA pair: a thread-block cluster of two CTAs, one
+// per SM.  The z1 chain (two dependent FP64 adds per element) is the
+// longest path of a short dot, and it ran ~20 % slower per element when
+// the z0 chain and the tail computation shared its SM (measured: ~174 SM
+// clocks per element in the one-CTA kernel against ~143 alone).  So the
+// producer CTA (rank 0) forms the products p_i, runs the z0 chains (every
+// partial sum s_i kept in shared memory) and the Two-Sum tails
+// t_i = err(s_{i-1} + p_i), one element per thread, and streams each chunk
+// of tails into the consumer's shared memory with st.async, whose
+// completion counts on a transaction mbarrier of the consumer; the consumer
+// CTA (rank 1) forms the product tails e_i and runs only the z1 chains, then
+// the block's subtree.  Every operation and operand is the one of
+// reduce_lat (p_i = RN(x_i y_i) is Two-Product's head), so the bits are the
+// same.  Waits are bounded (kPairSpin polls); a wait that runs out leaves
+// NaN in the block's result and counts in g_pair_timeouts.  Both CTAs meet
+// at a cluster barrier at the start (the consumer's mbarriers are
+// initialised by then) and at the end (the consumer outlives every store
+// into its shared memory).
+constexpr int kPairChunks = 12;                 // hand-over chunks (named barriers 1..kPairChunks)
+constexpr int kPairTail = kLatThreads - 32;     // producer warps 1.. compute tails
+constexpr long long kPairSpin = 1ll << 24;      // polls of an mbarrier before giving up
+constexpr int64_t kPairTargetClusters = 64;
+
+__device__ unsigned long long g_pair_timeouts;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, unsigned rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t a, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+// true once phase 0 of the mbarrier has completed; false after kPairSpin polls
+__device__ __forceinline__ bool mbar_wait0(uint32_t a) {
+    for (long long it = 0; it < kPairSpin; ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok) : "r"(a) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+// 8 bytes into the peer's shared memory, counted on the peer's mbarrier
+__device__ __forceinline__ void st_async8(uint32_t remote, double v, uint32_t remote_mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+                 ::"r"(remote), "l"(__double_as_longlong(v)), "r"(remote_mbar) : "memory");
+}
+
+// End of chunk c of a leaf of (rounded) length n8: chunks of 8, 16, 24,
+// 32, ... elements (multiples of 8), so that the z0 chain (~90 clocks per
+// element with its stores) and the tails stay ahead of the z1 chain (~143)
+// once it has started after the short first chunk; the last possible chunk
+// runs to the end of the leaf.
+__device__ __forceinline__ int pair_chunk_end(int c, int n8) {
+    return c >= kPairChunks - 1 ? n8 : min(8 * (c + 1) + 4 * c * (c + 1), n8);
+}
+
+// Shared memory of reduce_lat_pair (both CTAs, the same layout): PT [B][SP]
+// products p_i (producer), ET [B][SE] pairs (e_i, t_i) (consumer), SS [B][SP]
+// partial sums s_i (producer); rows padded with -0.0.
+size_t pair_smem(int B, int64_t L) {
+    const LatRows R(L);
+    return (2 * (size_t)B * R.SP + 2 * (size_t)B * R.SE) * sizeof(double);
+}
+
+template <bool DOT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_lat_pair(const __grid_constant__ RedArgs A) {
+    extern __shared__ __align__(16) double lat[];
+    __shared__ __align__(8) unsigned long long mbar[kPairChunks + 1];
+    __shared__ double r0[32];                    // consumer: the leaves' z0 results
+    griddep_wait();
+    griddep_release();
+    const unsigned rank = cluster_rank();
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int64_t b = blockIdx.x >> 1;           // the pair's block of B leaves
+    const int j = job_of(A.tab, A.njobs, b);
+    const int64_t e0 = A.tab.off(j), len = A.tab.off(j + 1) - e0;
+    const int64_t m = (len + A.L - 1) / A.L;
+    const int64_t leaf0 = (b - A.tab.b0(j)) * A.B;
+    const int nl = (int)min((int64_t)A.B, m - leaf0);
+    const int64_t base = e0 + leaf0 * A.L, end = e0 + len;
+    const int L = (int)A.L;
+    const LatRows R(A.L);
+    const int nel = (int)min((int64_t)nl * L, end - base);
+    double *PT = lat;                                                   // producer: p_i
+    double2 *ET = reinterpret_cast<double2 *>(lat + (size_t)A.B * R.SP);   // consumer: (e_i, t_i)
+    double *SS = lat + (size_t)A.B * R.SP + 2 * (size_t)A.B * R.SE;     // producer: s_i
+    const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
+    const int len0 = (int)min((int64_t)L, end - base);
+    const int n8 = (len0 + 7) & ~7;
+    int nch = 1;
+    while (nch < kPairChunks && pair_chunk_end(nch - 1, n8) < n8) ++nch;
+    if (rank == 1 && t <= nch) {
+        // phase bytes: the tails of chunk t's real elements; the z0 results (t = nch)
+        unsigned bytes = 8u * (unsigned)nl;
+        if (t < nch) {
+            const int i0 = t ? pair_chunk_end(t - 1, n8) : 0, i1 = pair_chunk_end(t, n8);
+            bytes = 0;
+            for (int r = 0; r < nl; ++r) {
+                const int rl = (int)min((int64_t)L, end - (base + (int64_t)r * L));
+                bytes += 8u * (unsigned)max(0, min(i1, rl) - i0);
+            }
+        }
+        mbar_init(smem_addr(&mbar[t]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect(smem_addr(&mbar[t]), bytes);
+    }
+    // the consumer's mbarriers are ready before any producer store; the
+    // terms follow in both CTAs (the consumer's z1 warp starts after its
+    // own CTA's terms and the first chunk of tails)
+    cluster_sync_all();
+    {
+        // terms, in both CTAs, all loads in flight first: the producer keeps
+        // p_i = RN(x_i y_i), the consumer e_i (Two-Product's tail, or the
+        // general product's z1)
+        double xv[kLatPer], xlv[kLatPer], yv[kLatPer], ylv[kLatPer];
+#pragma unroll
+        for (int u = 0; u < kLatPer; ++u) {
+            const int k = t + u * kLatThreads;
+            xv[u] = xlv[u] = yv[u] = ylv[u] = 0.0;
+            if (k < nel) {
+                const int64_t g = base + k;
+                xv[u] = A.xh[g];
+                if (!xd && (rank == 1 || !DOT)) xlv[u] = A.xl[g];
+                if (DOT) {
+                    yv[u] = A.yh[g];
+                    if (!yd && rank == 1) ylv[u] = A.yl[g];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLatPer; ++u) {
+            const int k = t + u * kLatThreads;
+            if (k < nel) {
+                const int r = k / L, i = k - r * L;
+                if (rank == 0) {
+                    PT[r * R.SP + i] = DOT ? __dmul_rn(xv[u], yv[u]) : xv[u];
+                } else if (DOT) {
+                    ET[r * R.SE + i].x = tf::apply(tf::OP_MUL, xv[u], xlv[u], xd, yv[u], ylv[u], yd).z1;
+                } else if (!xd) {
+                    ET[r * R.SE + i].x = xlv[u];
+                }
+            }
+        }
+        // -0.0 past the end of each leaf, up to L8 (the consumer pads both halves)
+        for (int q = t; q < nl * R.L8; q += kLatThreads) {
+            const int r = q / R.L8, i = q - r * R.L8;
+            if (base + (int64_t)r * L + i >= end || i >= L) {
+                if (rank == 0) PT[r * R.SP + i] = -0.0;
+                else ET[r * R.SE + i] = make_double2(-0.0, -0.0);
+            }
+        }
+    }
+    __syncthreads();
+    const int row = min(lane, nl - 1);
+    if (rank == 0) {
+        if (warp == 0) {                         // z0 chains; every s_i kept, in 16-byte pairs
+            const double2 *Pp = reinterpret_cast<const double2 *>(PT + row * R.SP);
+            double2 *Sp = reinterpret_cast<double2 *>(SS + row * R.SP);
+            double acc0 = 0.0;
+            for (int c = 0; c < nch; ++c) {
+                const int i1 = pair_chunk_end(c, n8);
+                for (int i = c ? pair_chunk_end(c - 1, n8) : 0; i < i1; i += 8) {
+                    double2 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = Pp[(i >> 1) + u];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        double2 sv;
+                        sv.x = acc0 = __dadd_rn(acc0, v[u].x);
+                        sv.y = acc0 = __dadd_rn(acc0, v[u].y);
+                        if (lane < nl) Sp[(i >> 1) + u] = sv;
+                    }
+                }
+                __syncwarp();
+                __threadfence_block();
+                bar_arrive(1 + c, kLatThreads);
+            }
+            if (lane < nl) st_async8(peer_addr(smem_addr(&r0[lane]), 1), acc0, peer_addr(smem_addr(&mbar[nch]), 1));
+        } else {                                 // tails t_i of each chunk, one element per thread
+            for (int c = 0; c < nch; ++c) {
+                bar_wait(1 + c, kLatThreads);
+                const int i0 = c ? pair_chunk_end(c - 1, n8) : 0, w = pair_chunk_end(c, n8) - i0;
+                const uint32_t rmb = peer_addr(smem_addr(&mbar[c]), 1);
+                for (int task = t - 32; task < nl * w; task += kPairTail) {
+                    const int r = task / w, i = i0 + task - r * w;
+                    const int rl = (int)min((int64_t)L, end - (base + (int64_t)r * L));
+                    if (i < rl) {
+                        const double sp = i ? SS[r * R.SP + i - 1] : 0.0;
+                        const double tv = tf::soft::sum_err(sp, PT[r * R.SP + i], SS[r * R.SP + i]);
+                        st_async8(peer_addr(smem_addr(&ET[r * R.SE + i].y), 1), tv, rmb);
+                    }
+                }
+            }
+        }
+    } else if (warp == 0) {                      // the z1 chains, then the block's subtree
+        const double2 *Q = ET + row * R.SE;
+        tf::d2 acc = {0.0, 0.0};
+        bool ok = true;
+        for (int c = 0; c < nch && ok; ++c) {
+            ok = mbar_wait0(smem_addr(&mbar[c]));
+            const int i1 = pair_chunk_end(c, n8);
+            for (int i = c ? pair_chunk_end(c - 1, n8) : 0; ok && i < i1; i += 8) {
+                double2 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = Q[i + u];
+                if (DOT || !xd) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(__dadd_rn(acc.z1, v[u].x), v[u].y);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(acc.z1, v[u].y);
+                }
+            }
+        }
+        ok = ok && mbar_wait0(smem_addr(&mbar[nch]));
+        ok = __all_sync(0xffffffffu, ok);
+        acc.z0 = ok ? r0[row] : __longlong_as_double(0x7FF8000000000000ll);
+        if (!ok) acc.z1 = acc.z0;
+        for (int st = 1; st < nl; st <<= 1) {
+            const double o0 = __shfl_down_sync(0xffffffffu, acc.z0, st);
+            const double o1 = __shfl_down_sync(0xffffffffu, acc.z1, st);
+            if ((lane & (2 * st - 1)) == 0 && lane + st < nl) acc = combine<false>(acc, {o0, o1});
+        }
+        if (lane == 0) {
+            if (!ok) atomicAdd(&g_pair_timeouts, 1ull);
+            if (A.tab.b0(j + 1) - A.tab.b0(j) == 1) write_result<false>(A, j, acc);
+            else { A.part0[b] = acc.z0; A.part1[b] = acc.z1; }
+        }
+    }
+    cluster_sync_all();
+}
+
+// Leaves per pair: the largest power of two <= 32 with B L <= kLatElems that
+// still leaves >= kPairTargetClusters pairs (two CTAs each) for the M leaves.
+int pair_group(int64_t L, int64_t M) {
+    int B = 32;
+    while (B > 1 && ((int64_t)B * L > kLatElems || (int64_t)B * kPairTargetClusters > M)) B >>= 1;
+    return B;
+}
+
 // One CTA of T threads per job with 0 or >= 2 blocks.  Thread t first
 // reduces the aligned group of G partials [tG, (t+1)G) (G = 2^g,
 // G T >= nb), which is a subtree, then the CTA reduces the group roots.
@@ -477,6 +733,35 @@ __global__ void __launch_bounds__(T) reduce_final(const __grid_constant__ RedArg
     }
     if (nb == 0) {
         if (t == 0) write_result<PLAIN>(A, j, {0.0, 0.0});
+        return;
+    }
+    if (nb <= 128) {
+        // one warp: lane l folds the aligned group of partials [4l, 4l + 4) in
+        // registers, then the group roots combine by shuffles (the same tree,
+        // without a barrier per level)
+        if (t >= 32) return;
+        const int cnt = (int)max((int64_t)0, min((int64_t)4, nb - 4 * (int64_t)t));
+        double q0[4] = {0.0, 0.0, 0.0, 0.0}, q1[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (i < cnt) { q0[i] = __ldcg(A.part0 + p0 + 4 * t + i); q1[i] = __ldcg(A.part1 + p0 + 4 * t + i); }
+#pragma unroll
+        for (int st = 1; st < 4; st <<= 1)
+#pragma unroll
+            for (int i = 0; i + st < 4; i += 2 * st)
+                if (i + st < cnt) {
+                    const tf::d2 r = combine<PLAIN>({q0[i], q1[i]}, {q0[i + st], q1[i + st]});
+                    q0[i] = r.z0;
+                    q1[i] = r.z1;
+                }
+        tf::d2 acc = {q0[0], q1[0]};
+        const int ng = (int)((nb + 3) / 4);
+        for (int st = 1; st < ng; st <<= 1) {
+            const double o0 = __shfl_down_sync(0xffffffffu, acc.z0, st);
+            const double o1 = __shfl_down_sync(0xffffffffu, acc.z1, st);
+            if ((t & (2 * st - 1)) == 0 && t + st < ng) acc = combine<PLAIN>(acc, {o0, o1});
+        }
+        if (t == 0) write_result<PLAIN>(A, j, acc);
         return;
     }
     int64_t G = 1;
@@ -579,7 +864,9 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
     for (int j = 0; j < njobs; ++j) M += (offs[j + 1] - offs[j] + L - 1) / L;
     // few leaves of moderate length: the latency schedule, one CTA per leaf
     const bool lat = M <= kLatMaxLeaves && L <= kLatMaxLeaf;
-    const int B = lat ? lat_group(L, M) : leaves_per_block(M);
+    // the twofold latency schedule runs on CTA pairs (reduce_lat_pair), the
+    // plain twin on single CTAs (reduce_lat)
+    const int B = lat ? (PLAIN ? lat_group(L, M) : pair_group(L, M)) : leaves_per_block(M);
     int64_t nblk = 0;
     bool need_final = false;
     for (int j = 0; j < njobs; ++j) {
@@ -626,7 +913,15 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
     A.narr = 1 + (xl != nullptr) + (DOT ? 1 + (yl != nullptr) : 0);
     A.C = chunk_of(B, A.narr, L);
     if (nblk > 0) {
-        if (lat) {
+        if (lat && !PLAIN) {
+            const size_t smem = pair_smem(B, L);
+            if (smem > 48 * 1024 && cudaFuncSetAttribute(reduce_lat_pair<DOT>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)smem) != cudaSuccess)
+                return TF_ECUDA;
+            if (tfh::launch_pdl(reduce_lat_pair<DOT>, 2 * nblk, kLatThreads, smem, s, A) != cudaSuccess)
+                return TF_ECUDA;
+        } else if (lat) {
             const size_t smem = lat_smem(B, L);
             if (smem > 48 * 1024 && cudaFuncSetAttribute(reduce_lat<DOT, PLAIN>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -134,6 +134,27 @@ def test_latency_schedule_leaf_sizes(L, n):
     assert_bits(T.plain_sum(dev(x), p=p), [O.reduce_plain(x, L=L)], f"L={L} plain sum")
 
 
+@pytest.mark.parametrize("n", [65536, 5000])
+@pytest.mark.parametrize("kinds", ["x", "y", "xy"])
+def test_latency_schedule_operand_kinds(n, kinds):
+    """The latency schedule (a CTA pair per block of leaves: products and z0
+    chains on one SM, product tails and z1 chains on the other) with tails
+    on x, on y or on both, and a sum with tails: the oracle's bits."""
+    x, y = synth.dot_uniform(n, seed=n + len(kinds))
+    xl = tails(x, 256) if "x" in kinds else None
+    yl = tails(y, 257) if "y" in kinds else None
+    e0, e1 = O.reduce(x, xl, y, yl)
+    z0, z1, fl = T.twofold_dot(dev(x), dev(y), None if xl is None else dev(xl), None if yl is None else dev(yl))
+    assert_bits(z0, [e0], f"{kinds} dot z0")
+    assert_bits(z1, [e1], f"{kinds} dot z1")
+    assert_flags(fl, [O.flag(e0, e1)], f"{kinds} dot flag")
+    if xl is not None:
+        s0, s1 = O.reduce(x, xl)
+        q0, q1, _ = T.twofold_sum(dev(x), dev(xl))
+        assert_bits(q0, [s0], "sum z0")
+        assert_bits(q1, [s1], "sum z1")
+
+
 def test_config_dot_65536_zero_tails_equal_dotted():
     """n = 65536 uniform[-1,1] seed 0: tails materialised as +0 and tails
     absent give the same bits, equal to the oracle."""
