@@ -37,6 +37,29 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &t
     t = soft::sum_err(a, b, s);
 }
 
+// Algorithm 1.2's result by Algorithm 1.1 on ordered operands: s = a + b,
+// then the Fast-Two-Sum tail small - (s - big) with big the operand of the
+// larger exponent field, which is the exact error (both subtractions are
+// exact when the exponent of big is at least that of small, gradual
+// underflow included); a zero error becomes +0, as Algorithm 1.2 returns.
+// Operands at or near the overflow threshold, Inf and NaN take the integer
+// tail (which follows the literal sequence there).  Two FP64 subtractions
+// and a few integer instructions in place of the integer tail's ~80: for
+// kernels whose integer pipes are busier than their FP64 pipe.
+__device__ __forceinline__ void two_sum_fp(double a, double b, double &s, double &t) {
+    s = __dadd_rn(a, b);
+    const uint64_t ua = bits_of(a), ub = bits_of(b);
+    const unsigned fa = (unsigned)(ua >> 52) & 0x7FF, fb = (unsigned)(ub >> 52) & 0x7FF;
+    if ((fa >= 2045) | (fb >= 2045)) {
+        t = soft::sum_err(a, b, s);
+        return;
+    }
+    const bool sw = fb > fa;
+    const double big = sw ? b : a, small = sw ? a : b;
+    const uint64_t ut = bits_of(__dsub_rn(small, __dsub_rn(s, big)));
+    t = from_bits((ut << 1) ? ut : 0);
+}
+
 // Algorithm 2.2 (Two-Diff): a - b -> d + t.  Steps (4),(5) in Shewchuk's
 // order (b# = b' - b, a# = a - a'), which makes a - b = d + t exact.  With
 // round-to-nearest every step of Two-Diff(a, b) is the negation-mirror of
@@ -192,7 +215,7 @@ __device__ __forceinline__ d2 rtf1(double x0, double x1) {
     uint64_t yz;
     const double z0 = soft::sqrt_rn_y(x0, &yz);
     double u0, u1;
-    two_sum(x0, x1, u0, u1);
+    two_sum_fp(x0, x1, u0, u1);
     double d;                                                // fma(-v0, v0, u0), packed
     uint64_t yv;
     const double v0 = soft::sqrt_rn_near(u0, x0, yz, &d, &yv);   // RPF1 on (u0, u1)

@@ -446,4 +446,48 @@ int64_t check_diff_err_near(uint64_t key, int64_t n, double *bad) {
     return nbad;
 }
 
+// The device's Fast-Two-Sum form of the Two-Sum tail (two_sum_fp in
+// tf_device.cuh: operands ordered by exponent field, small - (s - big), a
+// zero made +0; fields >= 2045 take sum_err) restated with host doubles,
+// against the literal Two-Sum sequence: random pairs over the whole range,
+// pairs with small gaps, cancellations, subnormals and special values.
+int64_t check_two_sum_fp(uint64_t key, int64_t n, double *bad) {
+    int64_t nbad = 0;
+    const double vals[] = {0.0, -0.0, INFINITY, -INFINITY, NAN, 1.0, -1.0, 1.7976931348623157e308,
+                           -1.7976931348623157e308, 4.9406564584124654e-324, -1e-310, 2.2250738585072014e-308};
+    const int nv = (int)(sizeof(vals) / sizeof(vals[0]));
+    for (int64_t i = 0; i < n + nv * nv; ++i) {
+        double a, b;
+        if (i >= n) {
+            a = vals[(i - n) / nv];
+            b = vals[(i - n) % nv];
+        } else {
+            a = rnd(key, 2 * i, 0, 2047);
+            b = rnd(key, 2 * i + 1, 0, 2047);
+            if (i % 3 == 1) b = -a * (1.0 + std::ldexp((double)(i % 97), -52));
+            if (i % 5 == 0) b = std::ldexp(a, -(int)(i % 70)) * (i & 8 ? -1.0 : 1.0);
+        }
+        volatile double s = a + b;
+        const double ref = literal_two_sum_tail(a, b);
+        const uint64_t ua = d2u(a), ub = d2u(b);
+        const unsigned fa = (unsigned)(ua >> 52) & 0x7FF, fb = (unsigned)(ub >> 52) & 0x7FF;
+        double got;
+        if ((fa >= 2045) | (fb >= 2045)) {
+            got = sum_err(a, b, s);
+        } else {
+            const bool sw = fb > fa;
+            const double big = sw ? b : a, small = sw ? a : b;
+            volatile double z = s - big;
+            volatile double tt = small - z;
+            const uint64_t ut = d2u(tt);
+            got = u2d((ut << 1) ? ut : 0);
+        }
+        if (!same(got, ref)) {
+            if (!nbad) { bad[0] = a; bad[1] = b; }
+            ++nbad;
+        }
+    }
+    return nbad;
+}
+
 }  // extern "C"

@@ -25,7 +25,7 @@ def H(tmp_path_factory):
         getattr(L, name).restype = i64
     for name in ("check_div_hard", "check_sqrt_hard", "check_div_by_root", "check_div_shared",
                  "check_sqrt_near", "check_scale_pow2", "check_remainder_specials", "check_div_by_near_root",
-                 "check_diff_err_near"):
+                 "check_diff_err_near", "check_two_sum_fp"):
         getattr(L, name).argtypes = [u64, i64, p]
         getattr(L, name).restype = i64
     L.soft_div.argtypes = [d, d]
@@ -82,6 +82,12 @@ def test_diff_err_matches_literal_two_diff(H):
     run(H, "check_diff_err", 13, 2_000_000, 900, 1150)
     run(H, "check_diff_err", 14, 1_000_000, 0, 2047)
     run(H, "check_diff_err", 15, 1_000_000, 1980, 2046)
+
+
+def test_fast_two_sum_form_matches_literal_two_sum(H):
+    """RTF1's Two-Sum of x0 and x1 as Fast-Two-Sum on exponent-ordered
+    operands (device two_sum_fp), restated on the host."""
+    run(H, "check_two_sum_fp", 33, 3_000_000)
 
 
 def test_sterbenz_diff_tail_matches_literal_two_diff(H):
