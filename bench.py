@@ -49,11 +49,11 @@ FALLBACK_HBM = 6800.0
 # fma probe, which runs at the issue rate).
 PIPE_PROBE = {"fp64": "dadd", "alu": "shf", "fmaheavy": "imad", "issue": "ffma"}
 PIPE_LOAD = {
-    "ew_chain": ({"fp64": 17.00, "alu": 726.97, "fmaheavy": 314.64, "issue": 1246.40}, "element",
+    "ew_chain": ({"fp64": 19.00, "alu": 670.04, "fmaheavy": 302.64, "issue": 1180.20}, "element",
                  "profiles/tf_jit_ew_chain_n2e28.md"),
     "horner": ({"fp64": 4.000, "alu": 129.40, "fmaheavy": 36.64, "issue": 194.72}, "point step",
                "profiles/horner_kernel_k5-30_2e24.md"),
-    "cond_dots": ({"fp64": 3.064, "alu": 145.56, "fmaheavy": 39.52, "issue": 211.08}, "element",
+    "cond_dots": ({"fp64": 3.564, "alu": 129.23, "fmaheavy": 35.49, "issue": 190.30}, "element",
                   "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
 }
 
@@ -74,10 +74,10 @@ HORNER_OPS_PER_STEP = 4 + 7              # MTF1.1 + ATF1.1
 # profiles/), scaled by the units a launch processes; None where the kernel
 # changed after its counters were taken.
 TRAFFIC_PER_UNIT = {
-    "ew_chain": (370.93e6 * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
+    "ew_chain": (370.14e6 * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
     "ew_chain_f32": ((536.904e6 + 130.459e6) * 16 / (1 << 28), "profiles/tf_jit_ew_chain_f32_n2e28.md"),
     "horner": (784.21e6 * 2 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
-    "cond_dots": (271.72e6 / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
+    "cond_dots": (271.68e6 / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
     "dot": (1.120256e6 / 65536, "profiles/reduce_lat_pair_dot_n65536.md"),
     "dot_f32": ((536.895e6 + 3.582e6) / (1 << 26), "profiles/red32_blocks_dot_f32_2e28.md"),
 }
@@ -87,7 +87,7 @@ TRAFFIC_PER_UNIT = {
 # a Horner step: MTF1.1 1 mul + 1 add, ATF1.1 2 add; a dotted dot element:
 # ATF1 3 add, the Two-Product on the integer pipes), the rest of their
 # arithmetic running on the integer pipes with the same bits.
-ALG_FP64 = {"ew_chain": 17, "horner": 4, "cond_dots": 3, "dot": 3}
+ALG_FP64 = {"ew_chain": 17, "horner": 4, "cond_dots": 3, "dot": 3}   # (the kernels issue a few more, see PIPE_LOAD)
 
 
 def measured_peaks():

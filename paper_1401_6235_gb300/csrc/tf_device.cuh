@@ -105,6 +105,14 @@ __device__ __forceinline__ d2 atf1(double x0, double x1, double y0, double y1) {
     return {s, __dadd_rn(__dadd_rn(x1, y1), e)};
 }
 
+// ATF1 with the Two-Sum tail from two_sum_fp (same bits; fewer integer
+// instructions for two more FP64 ones).
+__device__ __forceinline__ d2 atf1_fp(double x0, double x1, double y0, double y1) {
+    double s, e;
+    two_sum_fp(x0, y0, s, e);
+    return {s, __dadd_rn(__dadd_rn(x1, y1), e)};
+}
+
 // ATF1.1: z0 = x0 + y0; z1 = x1 + err(x0 + y0).
 __device__ __forceinline__ d2 atf11(double x0, double x1, double y0) {
     double s, e;

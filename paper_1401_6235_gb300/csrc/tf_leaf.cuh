@@ -20,13 +20,19 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
 }
 
 // acc = ATF1(acc, term) for one element (x1, y1 are +0 for dotted operands).
-template <bool DOT, bool XD, bool YD>
+// FP: the accumulation's Two-Sum tail by Fast-Two-Sum on ordered operands
+// (atf1_fp, same bits).  The dotted dot's step is bound by its integer
+// instructions (Two-Product and the Two-Sum tail, ~145 per element against
+// 3 FP64 ones), so one element in four takes that form, which balances the
+// two pipes; every other kind is bound by its FP64 instructions and keeps
+// the integer tail.
+template <bool DOT, bool XD, bool YD, bool FP = false>
 __device__ __forceinline__ void leaf_term(d2 &acc, double x0, double x1, double y0, double y1) {
     if constexpr (!DOT) {
         acc = XD ? atf11(acc.z0, acc.z1, x0) : atf1(acc.z0, acc.z1, x0, x1);
     } else {
         const d2 p = apply(OP_MUL, x0, x1, XD, y0, y1, YD);
-        acc = atf1(acc.z0, acc.z1, p.z0, p.z1);
+        acc = FP ? atf1_fp(acc.z0, acc.z1, p.z0, p.z1) : atf1(acc.z0, acc.z1, p.z0, p.z1);
     }
 }
 
@@ -49,7 +55,8 @@ __device__ __forceinline__ d2 leaf_walk(const double *X, const double *XL, const
             if (DOT) ld4(Y + i, y);
             if (DOT && !YD) ld4(YL + i, yl);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) leaf_term<DOT, XD, YD>(acc, x[u], xl[u], y[u], yl[u]);
+            for (int u = 0; u < 3; ++u) leaf_term<DOT, XD, YD>(acc, x[u], xl[u], y[u], yl[u]);
+            leaf_term<DOT, XD, YD, DOT && XD && YD>(acc, x[3], xl[3], y[3], yl[3]);
         }
     }
     for (; i < len; ++i)
