@@ -283,6 +283,16 @@ def measure_latencies(names=("dadd", "dmul", "dfma", "imad"), target_cycles=1e6)
         torch.cuda.synchronize()
         r = probe_rate(rec.cpu().numpy(), 32, iters)
         out[name] = {"cycles": 32.0 / r["op_per_clk_sm"], "iters": iters}
+    # a short reduction's critical loop: one 16-byte load and two dependent adds per element
+    op = T.PROBE_CHAIN_LDS | T.PROBE_LATENCY
+    T.pipe_probe(op, 1, sms, 32, rec)
+    torch.cuda.synchronize()
+    iters = max(2, int(target_cycles / (256 * 150)))
+    T.pipe_probe(op, iters, sms, 32, rec)
+    torch.cuda.synchronize()
+    r = probe_rate(rec.cpu().numpy(), 32, iters, ops_per_iter=256)
+    out["chain_lds_element"] = {"cycles": 32.0 / r["op_per_clk_sm"], "iters": iters,
+                                "what": "clocks per element of acc = (acc + e) + t with (e, t) loaded from shared memory"}
     return out
 
 

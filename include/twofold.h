@@ -532,6 +532,11 @@ int twofold_server_inject_failures(tf_server *s, int32_t every);
  * op | TF_PROBE_LATENCY (DADD, DMUL, DFMA, IMAD only) runs the same count as
  * one dependent chain per thread: with one warp per SM, 32 / (lane ops per
  * SM clock) is the latency of one instruction in SM clocks.
+ * TF_PROBE_LATENCY | TF_PROBE_CHAIN_LDS runs a short reduction's critical
+ * loop: per element one 16-byte shared-memory load and two dependent
+ * binary64 adds, iters x 256 elements per thread (not x 128 instructions):
+ * with one warp per SM, 32 x 2 / (lane ops per SM clock) is the clocks one
+ * element takes.
  * CTA b writes rec[4b .. 4b+3] (device int64 array of 4 * blocks, 8-byte
  * aligned): its SM id, its start and end SM clock (clock64), and a digest
  * of its chains.  Lane operations per SM clock on SM s = (threads x iters x
@@ -547,6 +552,7 @@ int twofold_server_inject_failures(tf_server *s, int32_t every);
 #define TF_PROBE_MULHI64 6
 #define TF_PROBE_MUFU 7
 #define TF_PROBE_I2F 8
+#define TF_PROBE_CHAIN_LDS 9
 #define TF_PROBE_LATENCY 0x100
 int twofold_pipe_probe(int32_t op, int64_t iters, int32_t blocks, int32_t threads, int64_t *rec, void *stream);
 

@@ -52,6 +52,39 @@ __device__ __forceinline__ void step(double (&d)[kChains], float (&f)[kChains], 
     }
 }
 
+// The latency-critical loop of a short reduction: acc = (acc + e_i) + t_i,
+// two dependent binary64 adds per element with the pair (e_i, t_i) from one
+// 16-byte shared-memory load (TF_PROBE_CHAIN_LDS; one chain per thread).
+__global__ void __launch_bounds__(1024) chain_lds_kernel(int64_t iters, long long *rec) {
+    __shared__ __align__(16) double2 S[256];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) S[k] = make_double2(1e-20 * k, -1e-21 * k);
+    __syncthreads();
+    double acc = 0.0;
+    const long long t0 = clock64();
+    for (int64_t it = 0; it < iters; ++it) {
+        for (int i = 0; i < 256; i += 8) {
+            double2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[u].x), "=d"(v[u].y)
+                             : "r"((unsigned)__cvta_generic_to_shared(&S[i + u])));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(acc) : "d"(v[u].x));
+                asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(acc) : "d"(v[u].y));
+            }
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        rec[4 * blockIdx.x + 0] = smid();
+        rec[4 * blockIdx.x + 1] = t0;
+        rec[4 * blockIdx.x + 2] = t1;
+        rec[4 * blockIdx.x + 3] = __double_as_longlong(acc);
+    }
+}
+
 template <int OP, bool LAT>
 __global__ void __launch_bounds__(1024) pipe_probe_kernel(int64_t iters, double a, double b, uint32_t m,
                                                           long long *rec) {
@@ -106,6 +139,10 @@ extern "C" int twofold_pipe_probe(int32_t op, int64_t iters, int32_t blocks, int
     if (!tfh::dptr_ok(rec)) return TF_EINVAL;
     long long *r = reinterpret_cast<long long *>(rec);
     cudaStream_t s = tfh::as_stream(stream);
+    if (op == (TF_PROBE_LATENCY | TF_PROBE_CHAIN_LDS)) {
+        chain_lds_kernel<<<blocks, threads, 0, s>>>(iters, r);
+        return cudaGetLastError() == cudaSuccess ? TF_OK : TF_ECUDA;
+    }
     const bool lat = (op & TF_PROBE_LATENCY) != 0;
     if (lat && op != (TF_PROBE_LATENCY | TF_PROBE_DADD) && op != (TF_PROBE_LATENCY | TF_PROBE_DMUL) &&
         op != (TF_PROBE_LATENCY | TF_PROBE_DFMA) && op != (TF_PROBE_LATENCY | TF_PROBE_IMAD))
