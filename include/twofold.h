@@ -326,6 +326,16 @@ int twofold_combine(const double *z0, const double *z1, int64_t m, tf_out out1, 
  * stream do not. */
 int twofold_dot_noalloc(tf_in x, tf_in y, int64_t n, tf_out out1, const tf_params *p, void *stream);
 
+/* The number of bounded device-side waits that ran out on the current
+ * device since the library was loaded (no paper counterpart: a diagnostic).
+ * The latency schedule of twofold_sum / twofold_dot (few leaves) runs each
+ * block of leaves on a pair of CTAs on two SMs, one handing chunks of its
+ * results to the other; the receiving CTA waits for each chunk a bounded
+ * number of polls, and if a wait runs out the block's result is NaN and
+ * this count grows.  Synchronous: it waits for the device's pending work
+ * in the legacy default stream.  TF_ECUDA if the count cannot be read. */
+int twofold_wait_timeouts(uint64_t *count);
+
 /* -------------------------------------------------------------- Horner
  *
  * p(x) = a_0 + a_1 x + ... + a_k x^k with dotted coefficients (ascending)

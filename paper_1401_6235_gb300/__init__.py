@@ -143,6 +143,7 @@ SIGNATURES = {
     "twofold_server_destroy": ([_P], ctypes.c_int),
     "twofold_server_inject_failures": ([_P, _I32], ctypes.c_int),
     "twofold_pipe_probe": ([_I32, _I64, _I32, _I32, _P, _P], ctypes.c_int),
+    "twofold_wait_timeouts": ([ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
 }
 
 _lib = None
@@ -581,3 +582,11 @@ def pipe_probe(op: int, iters: int, blocks: int, threads: int, rec=None, stream=
     rec = torch.empty(4 * blocks, dtype=torch.int64, device="cuda") if rec is None else rec
     _check(lib().twofold_pipe_probe(op, iters, blocks, threads, _dev(rec), _stream(stream)), "twofold_pipe_probe")
     return rec
+
+
+def wait_timeouts() -> int:
+    """Bounded device-side waits that ran out on the current device (see
+    twofold_wait_timeouts); 0 in a healthy run."""
+    c = ctypes.c_uint64()
+    _check(lib().twofold_wait_timeouts(ctypes.byref(c)), "twofold_wait_timeouts")
+    return int(c.value)

@@ -1066,6 +1066,17 @@ int noalloc_scratch(void **out) {
 
 }  // namespace
 
+extern "C" int twofold_wait_timeouts(uint64_t *count) {
+    if (!count) return TF_EINVAL;
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_pair_timeouts, sizeof v) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return TF_ECUDA;
+    }
+    *count = v;
+    return TF_OK;
+}
+
 extern "C" int twofold_dot_noalloc(tf_in x, tf_in y, int64_t n, tf_out out1, const tf_params *p,
                                    void *stream) {
     if (n < 0) return TF_EINVAL;

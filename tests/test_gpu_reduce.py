@@ -155,6 +155,14 @@ def test_latency_schedule_operand_kinds(n, kinds):
         assert_bits(q1, [s1], "sum z1")
 
 
+def test_latency_schedule_waits_never_ran_out():
+    """After the latency-schedule tests above, no CTA pair's bounded wait for
+    its partner's chunks has run out."""
+    x, y = synth.dot_uniform(65536, seed=3)
+    T.twofold_dot(dev(x), dev(y))
+    assert T.wait_timeouts() == 0
+
+
 def test_config_dot_65536_zero_tails_equal_dotted():
     """n = 65536 uniform[-1,1] seed 0: tails materialised as +0 and tails
     absent give the same bits, equal to the oracle."""
