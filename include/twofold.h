@@ -336,6 +336,16 @@ int twofold_dot_noalloc(tf_in x, tf_in y, int64_t n, tf_out out1, const tf_param
  * in the legacy default stream.  TF_ECUDA if the count cannot be read. */
 int twofold_wait_timeouts(uint64_t *count);
 
+/* Failure injection for testing the bounded waits above (no paper
+ * counterpart; no device fault is involved): from this call on, the latency
+ * schedule's producer CTAs do not send the tails of chunk `chunk` of each
+ * leaf (chunks count from 0), and the receiving CTAs give up waiting after
+ * 2^12 polls instead of 2^24; each affected block's result is NaN and
+ * twofold_wait_timeouts grows by one per block.  chunk = -1 turns injection
+ * off.  Process-wide, read when a sum or dot is launched.  Returns the
+ * previous setting, or TF_EINVAL for a chunk outside -1 .. 11. */
+int twofold_inject_pair_drop(int32_t chunk);
+
 /* -------------------------------------------------------------- Horner
  *
  * p(x) = a_0 + a_1 x + ... + a_k x^k with dotted coefficients (ascending)

@@ -144,6 +144,7 @@ SIGNATURES = {
     "twofold_server_inject_failures": ([_P, _I32], ctypes.c_int),
     "twofold_pipe_probe": ([_I32, _I64, _I32, _I32, _P, _P], ctypes.c_int),
     "twofold_wait_timeouts": ([ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "twofold_inject_pair_drop": ([_I32], ctypes.c_int),
 }
 
 _lib = None
@@ -590,3 +591,13 @@ def wait_timeouts() -> int:
     c = ctypes.c_uint64()
     _check(lib().twofold_wait_timeouts(ctypes.byref(c)), "twofold_wait_timeouts")
     return int(c.value)
+
+
+def inject_pair_drop(chunk: int) -> int:
+    """Failure injection for tests (twofold_inject_pair_drop): the latency
+    schedule's producers skip chunk `chunk` (-1: off); returns the previous
+    setting."""
+    r = lib().twofold_inject_pair_drop(chunk)
+    if r < -1:
+        _check(r, "twofold_inject_pair_drop")
+    return r

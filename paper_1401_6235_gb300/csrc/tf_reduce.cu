@@ -47,6 +47,8 @@ struct RedArgs {
     uint8_t *flags;
     tf::FlagCfg fc;
     int write_single;          // reduce_final writes jobs of one partial too (twofold_combine)
+    int pair_drop;             // latency schedule, failure injection: the chunk whose tails are not sent (-1: none)
+    long long pair_spin;       // latency schedule: polls of an mbarrier before a wait gives up
 };
 
 // Job of block b: the largest j with blk0[j] <= b (empty jobs own no block).
@@ -478,6 +480,7 @@ size_t lat_smem(int B, int64_t L) { return LatRows(L).bytes(B); }
 constexpr int kPairChunks = 12;                 // hand-over chunks (named barriers 1..kPairChunks)
 constexpr int kPairTail = kLatThreads - 32;     // producer warps 1.. compute tails
 constexpr long long kPairSpin = 1ll << 24;      // polls of an mbarrier before giving up
+constexpr long long kPairSpinInjected = 1ll << 12;   // ... while a failure is injected
 constexpr int64_t kPairTargetClusters = 64;
 
 __device__ unsigned long long g_pair_timeouts;
@@ -502,9 +505,9 @@ __device__ __forceinline__ void mbar_init(uint32_t a, unsigned count) {
 __device__ __forceinline__ void mbar_expect(uint32_t a, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
 }
-// true once phase 0 of the mbarrier has completed; false after kPairSpin polls
-__device__ __forceinline__ bool mbar_wait0(uint32_t a) {
-    for (long long it = 0; it < kPairSpin; ++it) {
+// true once phase 0 of the mbarrier has completed; false after `spin` polls
+__device__ __forceinline__ bool mbar_wait0(uint32_t a, long long spin) {
+    for (long long it = 0; it < spin; ++it) {
         uint32_t ok;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
@@ -655,6 +658,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
                 bar_wait(1 + c, kLatThreads);
                 const int i0 = c ? pair_chunk_end(c - 1, n8) : 0, w = pair_chunk_end(c, n8) - i0;
                 const uint32_t rmb = peer_addr(smem_addr(&mbar[c]), 1);
+                if (c == A.pair_drop) continue;   // injected failure: this chunk's tails never arrive
                 for (int task = t - 32; task < nl * w; task += kPairTail) {
                     const int r = task / w, i = i0 + task - r * w;
                     const int rl = (int)min((int64_t)L, end - (base + (int64_t)r * L));
@@ -669,9 +673,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
     } else if (warp == 0) {                      // the z1 chains, then the block's subtree
         const double2 *Q = ET + row * R.SE;
         tf::d2 acc = {0.0, 0.0};
+        // after a wait that gave up, the remaining chunks are still waited
+        // for (each bounded), so that every store the producer sent has
+        // landed before this CTA leaves
         bool ok = true;
-        for (int c = 0; c < nch && ok; ++c) {
-            ok = mbar_wait0(smem_addr(&mbar[c]));
+        for (int c = 0; c < nch; ++c) {
+            ok = mbar_wait0(smem_addr(&mbar[c]), A.pair_spin) && ok;
             const int i1 = pair_chunk_end(c, n8);
             for (int i = c ? pair_chunk_end(c - 1, n8) : 0; ok && i < i1; i += 8) {
                 double2 v[8];
@@ -686,7 +693,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
                 }
             }
         }
-        ok = ok && mbar_wait0(smem_addr(&mbar[nch]));
+        ok = mbar_wait0(smem_addr(&mbar[nch]), A.pair_spin) && ok;
         ok = __all_sync(0xffffffffu, ok);
         acc.z0 = ok ? r0[row] : __longlong_as_double(0x7FF8000000000000ll);
         if (!ok) acc.z1 = acc.z0;
@@ -830,6 +837,10 @@ int chunk_of(int B, int narr, int64_t L) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// twofold_inject_pair_drop: the chunk the latency schedule's producers skip
+// (-1: none); read at each launch.
+std::atomic<int> g_pair_drop{-1};
+
 // Workspace: [offs (njobs+1) | blk0 (njobs+1)] [part0 (nblk)] [part1 (nblk)].
 size_t ws_need(int njobs, int64_t nblk) {
     return align256(sizeof(int64_t) * 2 * (size_t)(njobs + 1)) + 2 * align256(sizeof(double) * (size_t)nblk);
@@ -886,6 +897,8 @@ int run(const double *xh, const double *xl, const double *yh, const double *yl, 
     A.njobs = njobs; A.L = L; A.B = B;
     A.out_hi = out_hi; A.out_lo = out_lo; A.flags = PLAIN ? nullptr : flags;
     A.fc = tfh::flag_cfg(p);
+    A.pair_drop = g_pair_drop.load(std::memory_order_relaxed);
+    A.pair_spin = A.pair_drop >= 0 ? kPairSpinInjected : kPairSpin;
     cudaStream_t s = tfh::as_stream(stream);
     const bool inl = njobs <= kInlineJobs;
     size_t need = 0;
@@ -1065,6 +1078,11 @@ int noalloc_scratch(void **out) {
 }
 
 }  // namespace
+
+extern "C" int twofold_inject_pair_drop(int32_t chunk) {
+    if (chunk < -1 || chunk >= kPairChunks) return TF_EINVAL;
+    return g_pair_drop.exchange(chunk);
+}
 
 extern "C" int twofold_wait_timeouts(uint64_t *count) {
     if (!count) return TF_EINVAL;

@@ -156,11 +156,39 @@ def test_latency_schedule_operand_kinds(n, kinds):
 
 
 def test_latency_schedule_waits_never_ran_out():
-    """After the latency-schedule tests above, no CTA pair's bounded wait for
-    its partner's chunks has run out."""
+    """In ordinary calls no CTA pair's bounded wait for its partner's chunks
+    runs out."""
+    before = T.wait_timeouts()
     x, y = synth.dot_uniform(65536, seed=3)
-    T.twofold_dot(dev(x), dev(y))
-    assert T.wait_timeouts() == 0
+    e0, e1 = O.reduce(x, None, y, None)
+    z0, z1, _ = T.twofold_dot(dev(x), dev(y))
+    assert_bits(z0, [e0], "z0")
+    assert_bits(z1, [e1], "z1")
+    assert T.wait_timeouts() == before
+
+
+@pytest.mark.parametrize("chunk", [0, 2])
+def test_latency_schedule_wait_that_runs_out(chunk):
+    """Failure injection on the host: the producers skip one chunk of tails,
+    so each consumer's bounded wait runs out.  Every block's result is NaN
+    (flag NONFINITE), the timeout count grows by the number of blocks (64
+    pairs at n = 65536), and the next ordinary call is correct again (the
+    context stays usable)."""
+    import numpy as np
+    x, y = synth.dot_uniform(65536, seed=4)
+    before = T.wait_timeouts()
+    prev = T.inject_pair_drop(chunk)
+    try:
+        z0, z1, fl = T.twofold_dot(dev(x), dev(y))
+        got = (host(z0)[0], host(z1)[0], int(host(fl)[0]))
+    finally:
+        T.inject_pair_drop(prev)
+    assert np.isnan(got[0]) and np.isnan(got[1]) and got[2] & T.NONFINITE
+    assert T.wait_timeouts() - before == 64
+    e0, e1 = O.reduce(x, None, y, None)
+    z0, z1, fl = T.twofold_dot(dev(x), dev(y))
+    assert_bits(z0, [e0], "z0 after")
+    assert_bits(z1, [e1], "z1 after")
 
 
 def test_config_dot_65536_zero_tails_equal_dotted():
