@@ -95,7 +95,10 @@ __device__ __forceinline__ void leaf_step(tf::d2 &acc, double x0, double x1, boo
 template <bool PLAIN>
 __device__ __forceinline__ tf::d2 combine(tf::d2 l, tf::d2 r) {
     if (PLAIN) return {__dadd_rn(l.z0, r.z0), 0.0};
-    return tf::atf1(l.z0, l.z1, r.z0, r.z1);
+    // the floating-point form of the Two-Sum tail (same bits): its latency,
+    // which a tree level waits for, is the shorter one (a 64-node final tree
+    // measured 2.8 against 3.1 us)
+    return tf::atf1_fp(l.z0, l.z1, r.z0, r.z1);
 }
 
 template <bool PLAIN>
@@ -516,27 +519,126 @@ __device__ __forceinline__ bool mbar_wait0(uint32_t a, long long spin) {
     }
     return false;
 }
+// true if phase 0 of the mbarrier has completed (one non-blocking test)
+__device__ __forceinline__ bool mbar_test0(uint32_t a) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(a) : "memory");
+    return ok != 0;
+}
+
+// The dependent chains of the pair kernel are written as inline PTX in a
+// fixed order: a batch's operands are loaded from shared memory one batch
+// ahead, issued right after the first addition of the batch before.  On
+// GB300 a binary64 add whose chain is interleaved with shared-memory loads
+// otherwise ran ~14 clocks per load above its 64-clock latency (~142 clocks
+// per z1 element against 128.5 with the operands in registers); in this
+// order ~131.
+__device__ __forceinline__ void lds2(double2 &v, uint32_t a) {
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+}
+// the same load without a compiler memory barrier (ordered after the
+// mbarrier waits, which are volatile too, and before nothing it must not pass)
+__device__ __forceinline__ void lds2v(double2 &v, uint32_t a) {
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+}
+__device__ __forceinline__ void sts2(uint32_t a, double x, double y) {
+    asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(x), "d"(y) : "memory");
+}
+__device__ __forceinline__ void dadd_to(double &acc, double v) {
+    asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(acc) : "d"(v));
+}
+
+// `bytes` (a multiple of 16) from this CTA's shared memory at `src` into the
+// peer's at `remote` (both 16-byte aligned), counted on the peer's mbarrier
+__device__ __forceinline__ void bulk_to_peer(uint32_t remote, uint32_t src, unsigned bytes, uint32_t remote_mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(remote), "r"(src), "r"(bytes), "r"(remote_mbar) : "memory");
+}
 // 8 bytes into the peer's shared memory, counted on the peer's mbarrier
 __device__ __forceinline__ void st_async8(uint32_t remote, double v, uint32_t remote_mbar) {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
                  ::"r"(remote), "l"(__double_as_longlong(v)), "r"(remote_mbar) : "memory");
 }
 
-// End of chunk c of a leaf of (rounded) length n8: chunks of 8, 16, 24,
-// 32, ... elements (multiples of 8), so that the z0 chain (~90 clocks per
-// element with its stores) and the tails stay ahead of the z1 chain (~143)
-// once it has started after the short first chunk; the last possible chunk
-// runs to the end of the leaf.
+// End of chunk c of a leaf of (rounded) length n8: 16, 32, 56, 96, 160,
+// 264, ... elements (each end the largest multiple of 8 <= 8 + 13/8 of the
+// one before).  The producer's z0 chain takes ~80 clocks per element and the
+// consumer's z1 chain ~140, so a chunk of this size is complete when the
+// consumer, started after the first chunk, reaches it.  (A first chunk of 8
+// measured 0.2 us slower: the second chunk's hand-over then stalled the
+// chain.)  The last possible chunk runs to the end of the leaf.  (A table: computing the
+// recurrence on the device put ~1.5 us of dependent integer work in front of
+// the terms.)
+__constant__ int kPairEnd[kPairChunks] = {16, 32, 56, 96, 160, 264, 432, 704, 1152, 1880, 2048, 2048};
 __device__ __forceinline__ int pair_chunk_end(int c, int n8) {
-    return c >= kPairChunks - 1 ? n8 : min(8 * (c + 1) + 4 * c * (c + 1), n8);
+    return c >= kPairChunks - 1 ? n8 : min(kPairEnd[c], n8);
 }
 
-// Shared memory of reduce_lat_pair (both CTAs, the same layout): PT [B][SP]
-// products p_i (producer), ET [B][SE] pairs (e_i, t_i) (consumer), SS [B][SP]
-// partial sums s_i (producer); rows padded with -0.0.
+// Shared memory of reduce_lat_pair: two regions of [B][SP] doubles.  The
+// producer keeps the products p_i in region 0 (overwritten by the tails t_i
+// once a chunk's z0 chain is done) and the partial sums s_i in region 1; the
+// consumer keeps e_i in region 0 and receives the t_i into region 1 (the
+// same offset in both CTAs, so the producer maps its own address).  Rows
+// padded with -0.0.
 size_t pair_smem(int B, int64_t L) {
     const LatRows R(L);
-    return (2 * (size_t)B * R.SP + 2 * (size_t)B * R.SE) * sizeof(double);
+    return 2 * (size_t)B * R.SP * sizeof(double);
+}
+
+// The consumer's z1 chain over one leaf row: e_i at shared address ea, t_i
+// at ta (TWO: acc = (acc + e_i) + t_i; else acc = acc + t_i, a sum of
+// binary64 values), chunk by chunk as the mbarriers at mb (8 bytes apart)
+// complete.  One flat loop over batches of 8 elements: the next batch is
+// loaded right after the batch's first add, and where it starts a new chunk
+// the (bounded) wait for that chunk comes just before its loads.  (Nested
+// per-chunk loops, or a non-blocking test of the next chunk in every batch,
+// measured 10-15 clocks per element slower.)  False if a wait gave up.
+template <bool TWO>
+__device__ __forceinline__ void z1_load(double2 (&e)[4], double2 (&tt)[4], uint32_t ea, uint32_t ta, int i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (TWO) lds2v(e[u], ea + 8 * i + 16 * u);
+        lds2v(tt[u], ta + 8 * i + 16 * u);
+    }
+}
+template <bool TWO>
+__device__ __forceinline__ bool z1_chain(uint32_t ea, uint32_t ta, uint32_t mb, int n8, int nch, long long spin,
+                                         double &acc) {
+    bool ok = mbar_wait0(mb, spin);
+    double2 ce[4], ct[4], ne[4], nt[4];
+    z1_load<TWO>(ce, ct, ea, ta, 0);
+    int c = 0, cend = pair_chunk_end(0, n8);
+    for (int i = 0; i < n8; i += 8) {
+        const int in = i + 8 < n8 ? i + 8 : i;   // the last batch reloads itself (unused)
+        dadd_to(acc, TWO ? ce[0].x : ct[0].x);
+        if (in == cend) {
+            ++c;
+            cend = pair_chunk_end(c, n8);
+            if (!mbar_test0(mb + 8 * c)) ok = mbar_wait0(mb + 8 * c, spin) && ok;
+        }
+        z1_load<TWO>(ne, nt, ea, ta, in);
+        if (TWO) {
+            dadd_to(acc, ct[0].x);
+            dadd_to(acc, ce[0].y);
+        }
+        dadd_to(acc, ct[0].y);
+#pragma unroll
+        for (int u = 1; u < 4; ++u) {
+            if (TWO) dadd_to(acc, ce[u].x);
+            dadd_to(acc, ct[u].x);
+            if (TWO) dadd_to(acc, ce[u].y);
+            dadd_to(acc, ct[u].y);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ce[u] = ne[u];
+            ct[u] = nt[u];
+        }
+    }
+    for (int k = c + 1; k < nch; ++k) ok = mbar_wait0(mb + 8 * k, spin) && ok;
+    return ok;
 }
 
 template <bool DOT>
@@ -558,37 +660,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
     const int L = (int)A.L;
     const LatRows R(A.L);
     const int nel = (int)min((int64_t)nl * L, end - base);
-    double *PT = lat;                                                   // producer: p_i
-    double2 *ET = reinterpret_cast<double2 *>(lat + (size_t)A.B * R.SP);   // consumer: (e_i, t_i)
-    double *SS = lat + (size_t)A.B * R.SP + 2 * (size_t)A.B * R.SE;     // producer: s_i
+    double *PT = lat;                            // producer: p_i, then t_i; consumer: e_i
+    double *SS = lat + (size_t)A.B * R.SP;       // producer: s_i; consumer: t_i (copied by the producer)
     const bool xd = A.xl == nullptr, yd = A.yl == nullptr;
     const int len0 = (int)min((int64_t)L, end - base);
     const int n8 = (len0 + 7) & ~7;
     int nch = 1;
     while (nch < kPairChunks && pair_chunk_end(nch - 1, n8) < n8) ++nch;
     if (rank == 1 && t <= nch) {
-        // phase bytes: the tails of chunk t's real elements; the z0 results (t = nch)
+        // phase bytes: the tails of chunk t of every row (-0.0 past a leaf's
+        // end); the z0 results (t = nch)
         unsigned bytes = 8u * (unsigned)nl;
-        if (t < nch) {
-            const int i0 = t ? pair_chunk_end(t - 1, n8) : 0, i1 = pair_chunk_end(t, n8);
-            bytes = 0;
-            for (int r = 0; r < nl; ++r) {
-                const int rl = (int)min((int64_t)L, end - (base + (int64_t)r * L));
-                bytes += 8u * (unsigned)max(0, min(i1, rl) - i0);
-            }
-        }
+        if (t < nch) bytes *= (unsigned)(pair_chunk_end(t, n8) - (t ? pair_chunk_end(t - 1, n8) : 0));
         mbar_init(smem_addr(&mbar[t]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         mbar_expect(smem_addr(&mbar[t]), bytes);
     }
-    // the consumer's mbarriers are ready before any producer store; the
-    // terms follow in both CTAs (the consumer's z1 warp starts after its
-    // own CTA's terms and the first chunk of tails)
+    // the consumer's mbarriers are ready before any producer copy; the
+    // terms follow in both CTAs
     cluster_sync_all();
+    const int row = min(lane, nl - 1);
     {
-        // terms, in both CTAs, all loads in flight first: the producer keeps
-        // p_i = RN(x_i y_i), the consumer e_i (Two-Product's tail, or the
-        // general product's z1)
+        // terms, all loads in flight first: the producer keeps p_i =
+        // RN(x_i y_i) (or x_i for a sum), the consumer e_i (the product's z1:
+        // Two-Product's tail, or the general product's; xl_i for a sum)
         double xv[kLatPer], xlv[kLatPer], yv[kLatPer], ylv[kLatPer];
 #pragma unroll
         for (int u = 0; u < kLatPer; ++u) {
@@ -596,8 +691,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
             xv[u] = xlv[u] = yv[u] = ylv[u] = 0.0;
             if (k < nel) {
                 const int64_t g = base + k;
-                xv[u] = A.xh[g];
-                if (!xd && (rank == 1 || !DOT)) xlv[u] = A.xl[g];
+                if (rank == 0 || DOT) xv[u] = A.xh[g];
+                if (!xd && rank == 1) xlv[u] = A.xl[g];
                 if (DOT) {
                     yv[u] = A.yh[g];
                     if (!yd && rank == 1) ylv[u] = A.yl[g];
@@ -609,101 +704,101 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
             const int k = t + u * kLatThreads;
             if (k < nel) {
                 const int r = k / L, i = k - r * L;
-                if (rank == 0) {
-                    PT[r * R.SP + i] = DOT ? __dmul_rn(xv[u], yv[u]) : xv[u];
-                } else if (DOT) {
-                    ET[r * R.SE + i].x = tf::apply(tf::OP_MUL, xv[u], xlv[u], xd, yv[u], ylv[u], yd).z1;
-                } else if (!xd) {
-                    ET[r * R.SE + i].x = xlv[u];
-                }
+                if (rank == 0) PT[r * R.SP + i] = DOT ? __dmul_rn(xv[u], yv[u]) : xv[u];
+                else if (DOT) PT[r * R.SP + i] = tf::apply(tf::OP_MUL, xv[u], xlv[u], xd, yv[u], ylv[u], yd).z1;
+                else if (!xd) PT[r * R.SP + i] = xlv[u];
             }
         }
-        // -0.0 past the end of each leaf, up to L8 (the consumer pads both halves)
+        // -0.0 past the end of each leaf, up to L8 (the tails there come from the producer)
         for (int q = t; q < nl * R.L8; q += kLatThreads) {
             const int r = q / R.L8, i = q - r * R.L8;
-            if (base + (int64_t)r * L + i >= end || i >= L) {
-                if (rank == 0) PT[r * R.SP + i] = -0.0;
-                else ET[r * R.SE + i] = make_double2(-0.0, -0.0);
-            }
+            if (base + (int64_t)r * L + i >= end || i >= L) PT[r * R.SP + i] = -0.0;
         }
     }
     __syncthreads();
-    const int row = min(lane, nl - 1);
     if (rank == 0) {
         if (warp == 0) {                         // z0 chains; every s_i kept, in 16-byte pairs
-            const double2 *Pp = reinterpret_cast<const double2 *>(PT + row * R.SP);
-            double2 *Sp = reinterpret_cast<double2 *>(SS + row * R.SP);
+            const uint32_t pa = smem_addr(PT + row * R.SP), sa = smem_addr(SS + row * R.SP);
             double acc0 = 0.0;
-            for (int c = 0; c < nch; ++c) {
-                const int i1 = pair_chunk_end(c, n8);
-                for (int i = c ? pair_chunk_end(c - 1, n8) : 0; i < i1; i += 8) {
-                    double2 v[4];
+            double2 cur[4], nxt[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) v[u] = Pp[(i >> 1) + u];
+            for (int u = 0; u < 4; ++u) lds2(cur[u], pa + 16 * u);
+            int c = 0, cend = pair_chunk_end(0, n8);
+            for (int i = 0; i < n8; i += 8) {
+                double sx, sy;
+                dadd_to(acc0, cur[0].x);
+                sx = acc0;
+                if (i + 8 < n8) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        double2 sv;
-                        sv.x = acc0 = __dadd_rn(acc0, v[u].x);
-                        sv.y = acc0 = __dadd_rn(acc0, v[u].y);
-                        if (lane < nl) Sp[(i >> 1) + u] = sv;
-                    }
+                    for (int u = 0; u < 4; ++u) lds2(nxt[u], pa + 8 * (i + 8) + 16 * u);
                 }
-                __syncwarp();
-                __threadfence_block();
-                bar_arrive(1 + c, kLatThreads);
+                dadd_to(acc0, cur[0].y);
+                sy = acc0;
+                if (lane < nl) sts2(sa + 8 * i, sx, sy);
+#pragma unroll
+                for (int u = 1; u < 4; ++u) {
+                    dadd_to(acc0, cur[u].x);
+                    sx = acc0;
+                    dadd_to(acc0, cur[u].y);
+                    sy = acc0;
+                    if (lane < nl) sts2(sa + 8 * i + 16 * u, sx, sy);
+                }
+                if (i + 8 == cend) {
+                    __syncwarp();
+                    __threadfence_block();
+                    bar_arrive(1 + c, kLatThreads);
+                    ++c;
+                    cend = pair_chunk_end(c, n8);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cur[u] = nxt[u];
             }
             if (lane < nl) st_async8(peer_addr(smem_addr(&r0[lane]), 1), acc0, peer_addr(smem_addr(&mbar[nch]), 1));
-        } else {                                 // tails t_i of each chunk, one element per thread
+        } else {
+            // tails t_i of each chunk, one element per thread, written over
+            // p_i (only this thread reads p_i once the chunk's z0 chain is
+            // done; -0.0 past a leaf's end); then one bulk copy per row into
+            // the consumer's t row
             for (int c = 0; c < nch; ++c) {
                 bar_wait(1 + c, kLatThreads);
                 const int i0 = c ? pair_chunk_end(c - 1, n8) : 0, w = pair_chunk_end(c, n8) - i0;
-                const uint32_t rmb = peer_addr(smem_addr(&mbar[c]), 1);
-                if (c == A.pair_drop) continue;   // injected failure: this chunk's tails never arrive
                 for (int task = t - 32; task < nl * w; task += kPairTail) {
                     const int r = task / w, i = i0 + task - r * w;
                     const int rl = (int)min((int64_t)L, end - (base + (int64_t)r * L));
+                    double tv = -0.0;
                     if (i < rl) {
                         const double sp = i ? SS[r * R.SP + i - 1] : 0.0;
-                        const double tv = tf::soft::sum_err(sp, PT[r * R.SP + i], SS[r * R.SP + i]);
-                        st_async8(peer_addr(smem_addr(&ET[r * R.SE + i].y), 1), tv, rmb);
+                        tv = tf::soft::sum_err(sp, PT[r * R.SP + i], SS[r * R.SP + i]);
                     }
+                    PT[r * R.SP + i] = tv;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_wait(kPairChunks + 1, kPairTail);
+                if (t == 32 && c != A.pair_drop) {   // pair_drop: injected failure, this chunk never arrives
+                    const uint32_t rmb = peer_addr(smem_addr(&mbar[c]), 1);
+                    for (int r = 0; r < nl; ++r)
+                        bulk_to_peer(peer_addr(smem_addr(SS + r * R.SP + i0), 1), smem_addr(PT + r * R.SP + i0),
+                                     8u * (unsigned)w, rmb);
                 }
             }
         }
     } else if (warp == 0) {                      // the z1 chains, then the block's subtree
-        const double2 *Q = ET + row * R.SE;
+        const uint32_t ea = smem_addr(PT + row * R.SP), ta = smem_addr(SS + row * R.SP), mb = smem_addr(&mbar[0]);
         tf::d2 acc = {0.0, 0.0};
-        // after a wait that gave up, the remaining chunks are still waited
-        // for (each bounded), so that every store the producer sent has
-        // landed before this CTA leaves
-        bool ok = true;
-        for (int c = 0; c < nch; ++c) {
-            ok = mbar_wait0(smem_addr(&mbar[c]), A.pair_spin) && ok;
-            const int i1 = pair_chunk_end(c, n8);
-            for (int i = c ? pair_chunk_end(c - 1, n8) : 0; ok && i < i1; i += 8) {
-                double2 v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = Q[i + u];
-                if (DOT || !xd) {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(__dadd_rn(acc.z1, v[u].x), v[u].y);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) acc.z1 = __dadd_rn(acc.z1, v[u].y);
-                }
-            }
-        }
-        ok = mbar_wait0(smem_addr(&mbar[nch]), A.pair_spin) && ok;
-        ok = __all_sync(0xffffffffu, ok);
-        acc.z0 = ok ? r0[row] : __longlong_as_double(0x7FF8000000000000ll);
-        if (!ok) acc.z1 = acc.z0;
+        const bool ok = (DOT || !xd) ? z1_chain<true>(ea, ta, mb, n8, nch, A.pair_spin, acc.z1)
+                                     : z1_chain<false>(ea, ta, mb, n8, nch, A.pair_spin, acc.z1);
+        // every chunk was waited for (each wait bounded), so every copy the
+        // producer sent has landed before this CTA leaves
+        const bool ok_all = __all_sync(0xffffffffu, mbar_wait0(smem_addr(&mbar[nch]), A.pair_spin) && ok);
+        acc.z0 = ok_all ? r0[row] : __longlong_as_double(0x7FF8000000000000ll);
+        if (!ok_all) acc.z1 = acc.z0;
         for (int st = 1; st < nl; st <<= 1) {
             const double o0 = __shfl_down_sync(0xffffffffu, acc.z0, st);
             const double o1 = __shfl_down_sync(0xffffffffu, acc.z1, st);
             if ((lane & (2 * st - 1)) == 0 && lane + st < nl) acc = combine<false>(acc, {o0, o1});
         }
         if (lane == 0) {
-            if (!ok) atomicAdd(&g_pair_timeouts, 1ull);
+            if (!ok_all) atomicAdd(&g_pair_timeouts, 1ull);
             if (A.tab.b0(j + 1) - A.tab.b0(j) == 1) write_result<false>(A, j, acc);
             else { A.part0[b] = acc.z0; A.part1[b] = acc.z1; }
         }
