@@ -667,6 +667,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
     const int n8 = (len0 + 7) & ~7;
     int nch = 1;
     while (nch < kPairChunks && pair_chunk_end(nch - 1, n8) < n8) ++nch;
+    // the terms' loads go out first (their latency covers the mbarrier
+    // set-up and the cluster barrier): the producer needs x_i (and y_i), the
+    // consumer x_i, y_i and the tails for a dot, xl_i for a sum
+    double xv[kLatPer], xlv[kLatPer], yv[kLatPer], ylv[kLatPer];
+#pragma unroll
+    for (int u = 0; u < kLatPer; ++u) {
+        const int k = t + u * kLatThreads;
+        xv[u] = xlv[u] = yv[u] = ylv[u] = 0.0;
+        if (k < nel) {
+            const int64_t g = base + k;
+            if (rank == 0 || DOT) xv[u] = A.xh[g];
+            if (!xd && rank == 1) xlv[u] = A.xl[g];
+            if (DOT) {
+                yv[u] = A.yh[g];
+                if (!yd && rank == 1) ylv[u] = A.yl[g];
+            }
+        }
+    }
     if (rank == 1 && t <= nch) {
         // phase bytes: the tails of chunk t of every row (-0.0 past a leaf's
         // end); the z0 results (t = nch)
@@ -681,24 +699,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
     cluster_sync_all();
     const int row = min(lane, nl - 1);
     {
-        // terms, all loads in flight first: the producer keeps p_i =
-        // RN(x_i y_i) (or x_i for a sum), the consumer e_i (the product's z1:
-        // Two-Product's tail, or the general product's; xl_i for a sum)
-        double xv[kLatPer], xlv[kLatPer], yv[kLatPer], ylv[kLatPer];
-#pragma unroll
-        for (int u = 0; u < kLatPer; ++u) {
-            const int k = t + u * kLatThreads;
-            xv[u] = xlv[u] = yv[u] = ylv[u] = 0.0;
-            if (k < nel) {
-                const int64_t g = base + k;
-                if (rank == 0 || DOT) xv[u] = A.xh[g];
-                if (!xd && rank == 1) xlv[u] = A.xl[g];
-                if (DOT) {
-                    yv[u] = A.yh[g];
-                    if (!yd && rank == 1) ylv[u] = A.yl[g];
-                }
-            }
-        }
+        // terms: the producer keeps p_i = RN(x_i y_i) (or x_i for a sum),
+        // the consumer e_i (the product's z1: Two-Product's tail, or the
+        // general product's; xl_i for a sum)
 #pragma unroll
         for (int u = 0; u < kLatPer; ++u) {
             const int k = t + u * kLatThreads;
