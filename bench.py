@@ -78,7 +78,7 @@ TRAFFIC_PER_UNIT = {
     "ew_chain_f32": ((536.904e6 + 130.459e6) * 16 / (1 << 28), "profiles/tf_jit_ew_chain_f32_n2e28.md"),
     "horner": (784.21e6 * 2 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
     "cond_dots": (271.68e6 / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
-    "dot": (1.120256e6 / 65536, "profiles/reduce_lat_pair_dot_n65536.md"),
+    "dot": (1.109248e6 / 65536, "profiles/reduce_lat_pair_dot_n65536.md"),
     "dot_f32": ((536.895e6 + 3.582e6) / (1 << 26), "profiles/red32_blocks_dot_f32_2e28.md"),
 }
 
