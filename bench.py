@@ -283,16 +283,22 @@ def measure_latencies(names=("dadd", "dmul", "dfma", "imad"), target_cycles=1e6)
         torch.cuda.synchronize()
         r = probe_rate(rec.cpu().numpy(), 32, iters)
         out[name] = {"cycles": 32.0 / r["op_per_clk_sm"], "iters": iters}
-    # a short reduction's critical loop: one 16-byte load and two dependent adds per element
-    op = T.PROBE_CHAIN_LDS | T.PROBE_LATENCY
-    T.pipe_probe(op, 1, sms, 32, rec)
-    torch.cuda.synchronize()
-    iters = max(2, int(target_cycles / (256 * 150)))
-    T.pipe_probe(op, iters, sms, 32, rec)
-    torch.cuda.synchronize()
-    r = probe_rate(rec.cpu().numpy(), 32, iters, ops_per_iter=256)
-    out["chain_lds_element"] = {"cycles": 32.0 / r["op_per_clk_sm"], "iters": iters,
-                                "what": "clocks per element of acc = (acc + e) + t with (e, t) loaded from shared memory"}
+    # a short reduction's critical loop: one 16-byte load and two dependent
+    # adds per element, in the compiler's order and in the fixed order of the
+    # CTA-pair reduction's chains
+    for key, form, what in (
+            ("chain_lds_element", T.PROBE_CHAIN_LDS,
+             "clocks per element of acc = (acc + e) + t with (e, t) loaded from shared memory"),
+            ("chain_ahead_element", T.PROBE_CHAIN_AHEAD,
+             "the same, loads and adds in a fixed order: the next 8 elements' loads after the first add of the 8 before")):
+        op = form | T.PROBE_LATENCY
+        T.pipe_probe(op, 1, sms, 32, rec)
+        torch.cuda.synchronize()
+        iters = max(2, int(target_cycles / (256 * 150)))
+        T.pipe_probe(op, iters, sms, 32, rec)
+        torch.cuda.synchronize()
+        r = probe_rate(rec.cpu().numpy(), 32, iters, ops_per_iter=256)
+        out[key] = {"cycles": 32.0 / r["op_per_clk_sm"], "iters": iters, "what": what}
     return out
 
 

@@ -556,7 +556,9 @@ int twofold_server_inject_failures(tf_server *s, int32_t every);
  * loop: per element one 16-byte shared-memory load and two dependent
  * binary64 adds, iters x 256 elements per thread (not x 128 instructions):
  * with one warp per SM, 32 x 2 / (lane ops per SM clock) is the clocks one
- * element takes.
+ * element takes.  TF_PROBE_LATENCY | TF_PROBE_CHAIN_AHEAD runs the same loop
+ * with its loads and adds in a fixed order, each 8 elements' loads issued
+ * right after the first add of the 8 before.
  * CTA b writes rec[4b .. 4b+3] (device int64 array of 4 * blocks, 8-byte
  * aligned): its SM id, its start and end SM clock (clock64), and a digest
  * of its chains.  Lane operations per SM clock on SM s = (threads x iters x
@@ -573,6 +575,7 @@ int twofold_server_inject_failures(tf_server *s, int32_t every);
 #define TF_PROBE_MUFU 7
 #define TF_PROBE_I2F 8
 #define TF_PROBE_CHAIN_LDS 9
+#define TF_PROBE_CHAIN_AHEAD 10
 #define TF_PROBE_LATENCY 0x100
 int twofold_pipe_probe(int32_t op, int64_t iters, int32_t blocks, int32_t threads, int64_t *rec, void *stream);
 

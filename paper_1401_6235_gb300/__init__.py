@@ -570,7 +570,7 @@ def plain_horner_batched(coefs, coef_offs, ks, x, x_offs, out=None, ws=None, str
 
 PROBE_DADD, PROBE_DMUL, PROBE_DFMA, PROBE_FFMA = 0, 1, 2, 3
 PROBE_IMAD, PROBE_SHF, PROBE_MULHI64, PROBE_MUFU, PROBE_I2F = 4, 5, 6, 7, 8
-PROBE_CHAIN_LDS, PROBE_LATENCY = 9, 0x100
+PROBE_CHAIN_LDS, PROBE_CHAIN_AHEAD, PROBE_LATENCY = 9, 10, 0x100
 #: lane instructions per thread per loop iteration of a probe (8 chains x 16 rounds)
 PROBE_OPS_PER_ITER = 128
 

@@ -85,6 +85,47 @@ __global__ void __launch_bounds__(1024) chain_lds_kernel(int64_t iters, long lon
     }
 }
 
+// The same loop in a fixed order (TF_PROBE_CHAIN_AHEAD): loads and adds as
+// inline PTX, the next 8 elements' loads issued right after the first add
+// of the 8 before (the order of the CTA-pair reduction's chains).
+__global__ void __launch_bounds__(1024) chain_ahead_kernel(int64_t iters, long long *rec) {
+    __shared__ __align__(16) double2 S[256];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) S[k] = make_double2(1e-20 * k, -1e-21 * k);
+    __syncthreads();
+    const unsigned base = (unsigned)__cvta_generic_to_shared(S);
+    double acc = 0.0;
+    double2 cur[8], nxt[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(cur[u].x), "=d"(cur[u].y) : "r"(base + 16 * u));
+    const long long t0 = clock64();
+    for (int64_t it = 0; it < iters; ++it) {
+        for (int i = 0; i < 256; i += 8) {
+            const unsigned na = base + 16 * ((i + 8) & 255);
+            asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(acc) : "d"(cur[0].x));
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(nxt[u].x), "=d"(nxt[u].y) : "r"(na + 16 * u));
+            asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(acc) : "d"(cur[0].y));
+#pragma unroll
+            for (int u = 1; u < 8; ++u) {
+                asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(acc) : "d"(cur[u].x));
+                asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(acc) : "d"(cur[u].y));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        rec[4 * blockIdx.x + 0] = smid();
+        rec[4 * blockIdx.x + 1] = t0;
+        rec[4 * blockIdx.x + 2] = t1;
+        rec[4 * blockIdx.x + 3] = __double_as_longlong(acc);
+    }
+}
+
 template <int OP, bool LAT>
 __global__ void __launch_bounds__(1024) pipe_probe_kernel(int64_t iters, double a, double b, uint32_t m,
                                                           long long *rec) {
@@ -141,6 +182,10 @@ extern "C" int twofold_pipe_probe(int32_t op, int64_t iters, int32_t blocks, int
     cudaStream_t s = tfh::as_stream(stream);
     if (op == (TF_PROBE_LATENCY | TF_PROBE_CHAIN_LDS)) {
         chain_lds_kernel<<<blocks, threads, 0, s>>>(iters, r);
+        return cudaGetLastError() == cudaSuccess ? TF_OK : TF_ECUDA;
+    }
+    if (op == (TF_PROBE_LATENCY | TF_PROBE_CHAIN_AHEAD)) {
+        chain_ahead_kernel<<<blocks, threads, 0, s>>>(iters, r);
         return cudaGetLastError() == cudaSuccess ? TF_OK : TF_ECUDA;
     }
     const bool lat = (op & TF_PROBE_LATENCY) != 0;

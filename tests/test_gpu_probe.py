@@ -43,6 +43,7 @@ def test_rates_within_the_pipes_limits(torch):
     assert 8 < lat["dadd"]["cycles"] < 500 and 1 < lat["imad"]["cycles"] < 50
     # two dependent adds per element: at least twice the add's latency
     assert 2 * lat["dadd"]["cycles"] * 0.95 < lat["chain_lds_element"]["cycles"] < 1000
+    assert 2 * lat["dadd"]["cycles"] * 0.95 < lat["chain_ahead_element"]["cycles"] < 1000
 
 
 def test_bad_arguments_are_rejected(torch):
