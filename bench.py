@@ -53,7 +53,7 @@ PIPE_LOAD = {
                  "profiles/tf_jit_ew_chain_n2e28.md"),
     "horner": ({"fp64": 4.000, "alu": 129.40, "fmaheavy": 36.64, "issue": 194.72}, "point step",
                "profiles/horner_kernel_k5-30_2e24.md"),
-    "cond_dots": ({"fp64": 3.564, "alu": 129.23, "fmaheavy": 35.49, "issue": 190.30}, "element",
+    "cond_dots": ({"fp64": 3.607, "alu": 128.06, "fmaheavy": 35.17, "issue": 188.85}, "element",
                   "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
 }
 
@@ -77,7 +77,7 @@ TRAFFIC_PER_UNIT = {
     "ew_chain": (370.14e6 * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
     "ew_chain_f32": ((536.904e6 + 130.459e6) * 16 / (1 << 28), "profiles/tf_jit_ew_chain_f32_n2e28.md"),
     "horner": (784.21e6 * 2 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
-    "cond_dots": (271.68e6 / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
+    "cond_dots": ((268.59e6 + 3.30e6) / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
     "dot": (1.109248e6 / 65536, "profiles/reduce_lat_pair_dot_n65536.md"),
     "dot_f32": ((536.895e6 + 3.582e6) / (1 << 26), "profiles/red32_blocks_dot_f32_2e28.md"),
 }
