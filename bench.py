@@ -49,7 +49,7 @@ FALLBACK_HBM = 6800.0
 # fma probe, which runs at the issue rate).
 PIPE_PROBE = {"fp64": "dadd", "alu": "shf", "fmaheavy": "imad", "issue": "ffma"}
 PIPE_LOAD = {
-    "ew_chain": ({"fp64": 19.00, "alu": 670.04, "fmaheavy": 302.64, "issue": 1180.20}, "element",
+    "ew_chain": ({"fp64": 21.00, "alu": 612.04, "fmaheavy": 286.65, "issue": 1106.22}, "element",
                  "profiles/tf_jit_ew_chain_n2e28.md"),
     "horner": ({"fp64": 4.000, "alu": 129.40, "fmaheavy": 36.64, "issue": 194.72}, "point step",
                "profiles/horner_kernel_k5-30_2e24.md"),
@@ -74,7 +74,7 @@ HORNER_OPS_PER_STEP = 4 + 7              # MTF1.1 + ATF1.1
 # profiles/), scaled by the units a launch processes; None where the kernel
 # changed after its counters were taken.
 TRAFFIC_PER_UNIT = {
-    "ew_chain": (370.14e6 * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
+    "ew_chain": ((284.63e6 + 87.02e6) * 64 / (1 << 28), "profiles/tf_jit_ew_chain_n2e28.md"),
     "ew_chain_f32": ((536.904e6 + 130.459e6) * 16 / (1 << 28), "profiles/tf_jit_ew_chain_f32_n2e28.md"),
     "horner": (784.21e6 * 2 / (1 << 26), "profiles/horner_kernel_k5-30_2e24.md"),
     "cond_dots": ((268.59e6 + 3.30e6) / (1 << 24), "profiles/reduce_blocks_cond_dots_4096x2e16.md"),
