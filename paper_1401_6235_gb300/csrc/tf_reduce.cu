@@ -469,17 +469,18 @@ size_t lat_smem(int B, int64_t L) { return LatRows(L).bytes(B); }
 // clocks per element in the one-CTA kernel against ~143 alone).  So the
 // producer CTA (rank 0) forms the products p_i, runs the z0 chains (every
 // partial sum s_i kept in shared memory) and the Two-Sum tails
-// t_i = err(s_{i-1} + p_i), one element per thread, and streams each chunk
-// of tails into the consumer's shared memory with st.async, whose
-// completion counts on a transaction mbarrier of the consumer; the consumer
-// CTA (rank 1) forms the product tails e_i and runs only the z1 chains, then
-// the block's subtree.  Every operation and operand is the one of
-// reduce_lat (p_i = RN(x_i y_i) is Two-Product's head), so the bits are the
-// same.  Waits are bounded (kPairSpin polls); a wait that runs out leaves
-// NaN in the block's result and counts in g_pair_timeouts.  Both CTAs meet
-// at a cluster barrier at the start (the consumer's mbarriers are
-// initialised by then) and at the end (the consumer outlives every store
-// into its shared memory).
+// t_i = err(s_{i-1} + p_i), one element per thread, written over p_i, and
+// sends each chunk of tails into the consumer's shared memory with one bulk
+// copy per leaf row, whose completion counts on a transaction mbarrier of
+// the consumer; the consumer CTA (rank 1) forms the product tails e_i and
+// runs only the z1 chains, then the block's subtree.  Every operation and
+// operand is the one of reduce_lat (p_i = RN(x_i y_i) is Two-Product's
+// head), so the bits are the same.  Waits are bounded (kPairSpin polls); a
+// wait that runs out leaves NaN in the block's result and counts in
+// g_pair_timeouts.  Both CTAs meet at a cluster barrier at the start (the
+// consumer's mbarriers are initialised by then) and at the end (the
+// consumer outlives every copy into its shared memory, the producer every
+// copy out of its own).
 constexpr int kPairChunks = 12;                 // hand-over chunks (named barriers 1..kPairChunks)
 constexpr int kPairTail = kLatThreads - 32;     // producer warps 1.. compute tails
 constexpr long long kPairSpin = 1ll << 24;      // polls of an mbarrier before giving up
