@@ -535,12 +535,13 @@ __device__ __forceinline__ bool mbar_test0(uint32_t a) {
 // GB300 a binary64 add whose chain is interleaved with shared-memory loads
 // otherwise ran ~14 clocks per load above its 64-clock latency (~142 clocks
 // per z1 element against 128.5 with the operands in registers); in this
-// order ~131.
+// order ~134 in the kernel.
 __device__ __forceinline__ void lds2(double2 &v, uint32_t a) {
     asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
 }
-// the same load without a compiler memory barrier (ordered after the
-// mbarrier waits, which are volatile too, and before nothing it must not pass)
+// the same load without a compiler memory barrier: volatile asm keeps its
+// place after the (volatile) mbarrier waits, and nothing later depends on
+// its order against other memory accesses
 __device__ __forceinline__ void lds2v(double2 &v, uint32_t a) {
     asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
 }
@@ -569,9 +570,9 @@ __device__ __forceinline__ void st_async8(uint32_t remote, double v, uint32_t re
 // consumer's z1 chain ~140, so a chunk of this size is complete when the
 // consumer, started after the first chunk, reaches it.  (A first chunk of 8
 // measured 0.2 us slower: the second chunk's hand-over then stalled the
-// chain.)  The last possible chunk runs to the end of the leaf.  (A table: computing the
-// recurrence on the device put ~1.5 us of dependent integer work in front of
-// the terms.)
+// chain.)  The last possible chunk runs to the end of the leaf.  (A table:
+// computing the recurrence on the device put ~1.5 us of dependent integer
+// work in front of the terms.)
 __constant__ int kPairEnd[kPairChunks] = {16, 32, 56, 96, 160, 264, 432, 704, 1152, 1880, 2048, 2048};
 __device__ __forceinline__ int pair_chunk_end(int c, int n8) {
     return c >= kPairChunks - 1 ? n8 : min(kPairEnd[c], n8);
