@@ -804,8 +804,16 @@ def workload_serve(args, rank, world, dist_on):
         h = srv._h
         tid = ctypes.c_uint64()
         info = T.tf_request_info()
-        for q in structs[:50]:                       # warm the server, the allocator and the kernels
-            submit_c(h, ctypes.byref(q), ctypes.byref(tid))
+        # warm the server, the allocator and the kernels: the first 50 requests
+        # and the largest of each kind (a large elementwise request builds the
+        # specialised chain kernel, ~0.2-0.9 s on first use)
+        warm = list(range(min(50, nreq)))
+        for kd in ("dot", "sum", "horner", "ew"):
+            idx = np.flatnonzero(kinds == kd)
+            if idx.size:
+                warm.append(int(idx[np.argmax(sizes[idx])]))
+        for i in warm:
+            submit_c(h, ctypes.byref(structs[i]), ctypes.byref(tid))
             wait_c(h, tid.value, -1, ctypes.byref(info))
         for rate, nr in zip(rates, per_rate):
             arrive = np.cumsum(rng.exponential(1.0 / rate, nr))
