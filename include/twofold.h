@@ -96,7 +96,7 @@ typedef enum {
     TF_EINVAL = -1,        /* bad argument (NULL, misaligned, n < 0, bad program, ...) */
     TF_ENOSPC = -2,        /* workspace too small                                     */
     TF_ECUDA = -3,         /* CUDA launch / runtime error                             */
-    TF_ETIMEOUT = -4,      /* a bounded wait (on the device or the host) gave up      */
+    TF_ETIMEOUT = -4,      /* a bounded device-side wait gave up                      */
     TF_EUNSUPPORTED = -5   /* valid request outside the library's limits             */
 } tf_status;
 
@@ -166,23 +166,14 @@ int twofold_ew(const int32_t *prog, int32_t nprog, const tf_in *in, int32_t nin,
 /* Runtime specialisation of elementwise programs: for n >= 2^20 (automatic
  * mode) twofold_ew and twofold_ew_f32 run a straight-line kernel of the
  * program, compiled once per distinct program (and operand kinds and flag
- * mode) by the runtime compiler for this GPU from the library's own device
- * code, and cached for the process; its results are the generic kernels'
- * bits.  In automatic mode the first call of a program starts the build on a
- * background thread (0.2-0.9 s) and runs on the generic kernels, as do the
- * calls until the build is done, so no call waits for the compiler; at mode 2
- * (every size) a call builds the kernel first if it is not built yet.  A
- * program that cannot be compiled runs on the generic kernels.
- * twofold_ew_jit sets the mode (0 off, 1 automatic, 2 at every size; -1 only
- * queries), returns the previous one (the initial mode is $TWOFOLD_JIT when
- * set, else 1), and reports how many kernels were built and failed so far
- * (either pointer may be NULL).  No paper counterpart. */
+ * mode) at its first such call by the runtime compiler for this GPU from the
+ * library's own device code, and cached for the process; its results are the
+ * generic kernels' bits.  A program that cannot be compiled runs on the
+ * generic kernels.  twofold_ew_jit sets the mode (0 off, 1 automatic, 2 at
+ * every size; -1 only queries), returns the previous one (the initial mode is
+ * $TWOFOLD_JIT when set, else 1), and reports how many kernels were built
+ * and failed so far (either pointer may be NULL).  No paper counterpart. */
 int twofold_ew_jit(int32_t mode, int64_t *built, int64_t *failed);
-
-/* Waits until no specialised-kernel build started by the automatic mode is
- * pending (at most timeout_ms milliseconds; < 0 means 60 s).  TF_OK, or
- * TF_ETIMEOUT when builds were still running. */
-int twofold_ew_jit_wait(int64_t timeout_ms);
 
 /* Plain binary64 twin of twofold_ew: the same program on the hi arrays
  * only (in: HOST array of nin device pointers), out[i] = the plain result

@@ -111,7 +111,6 @@ SIGNATURES = {
     "plain_arith": ([_I32], ctypes.c_int),
     "twofold_ew_f32": ([_P, _I32, _P, _I32, _I64, tf_out_f32, _PP, _P], ctypes.c_int),
     "twofold_ew_jit": ([_I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
-    "twofold_ew_jit_wait": ([_I64], ctypes.c_int),
     "plain_ew_f32": ([_P, _I32, _P, _I32, _I64, _P, _P], ctypes.c_int),
     "twofold_sum_f32": ([tf_in_f32, _I64, tf_out_f32, _PP, _P, _SZ, _P], ctypes.c_int),
     "twofold_dot_f32": ([tf_in_f32, tf_in_f32, _I64, tf_out_f32, _PP, _P, _SZ, _P], ctypes.c_int),
@@ -383,15 +382,6 @@ def jit_mode(mode: int = -1):
     if prev < 0:
         raise TwofoldError(prev, "twofold_ew_jit")
     return prev, b.value, f.value
-
-
-def jit_wait(timeout_ms: int = 60000) -> bool:
-    """Waits for the specialised-kernel builds that the automatic mode started
-    in the background (twofold_ew_jit_wait); True when none is pending."""
-    r = lib().twofold_ew_jit_wait(timeout_ms)
-    if r not in (TF_OK, TF_ETIMEOUT):
-        raise TwofoldError(r, "twofold_ew_jit_wait")
-    return r == TF_OK
 
 
 PLAIN_NATIVE, PLAIN_INTEGER = 0, 1

@@ -11,17 +11,12 @@
 // at build time), loaded with cudaLibraryLoadData and cached.  The
 // arithmetic is the library's own device code, so the bits are those of the
 // generic kernels; any failure to build leaves the call on them.
-#include <chrono>
-#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <deque>
 #include <mutex>
 #include <string>
-#include <thread>
 #include <unordered_map>
-#include <unordered_set>
 
 #include <nvrtc.h>
 
@@ -40,9 +35,7 @@ constexpr int kThreads = 128;
 int elems_of(const Prog &p) { return p.is_f32 ? 2 : 1; }
 
 std::mutex g_mu;
-std::condition_variable g_cv;                               // a build finished
 std::unordered_map<std::string, cudaKernel_t> g_cache;     // nullptr: failed to build
-std::unordered_set<std::string> g_pending;                  // builds queued or running
 int g_mode = -1;                                            // -1: read TWOFOLD_JIT once
 int64_t g_built = 0, g_failed = 0;
 
@@ -208,64 +201,6 @@ cudaKernel_t build(const Prog &p) {
     return k;
 }
 
-// Records a finished build (g_mu held).
-void finish_locked(const std::string &key, cudaKernel_t k) {
-    g_cache[key] = k;
-    if (k) ++g_built;
-    else ++g_failed;
-    g_pending.erase(key);
-    g_cv.notify_all();
-}
-
-// The background builder of the automatic mode: one thread, started at the
-// first queued build, taking builds in order.  Its owner is a function-local
-// static, destroyed at exit before the library's other state: it lets the
-// build in progress finish and joins the thread.
-struct Builder {
-    struct Job {
-        std::string key;
-        Prog prog;
-        int device;
-    };
-    std::deque<Job> queue;
-    bool stop = false;
-    std::thread worker;
-    void run() {
-        std::unique_lock<std::mutex> g(g_mu);
-        for (;;) {
-            g_cv.wait(g, [&] { return stop || !queue.empty(); });
-            if (stop) return;
-            Job j = std::move(queue.front());
-            queue.pop_front();
-            g.unlock();
-            cudaSetDevice(j.device);
-            const cudaKernel_t k = build(j.prog);
-            g.lock();
-            finish_locked(j.key, k);
-        }
-    }
-    ~Builder() {
-        {
-            std::lock_guard<std::mutex> g(g_mu);
-            stop = true;
-            g_cv.notify_all();
-        }
-        if (worker.joinable()) worker.join();
-    }
-};
-
-// Queues the build of p under `key` (g_mu held; the key is not cached and
-// not pending).
-void enqueue_locked(const std::string &key, const Prog &p) {
-    static Builder b;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) (void)cudaGetLastError();
-    b.queue.push_back({key, p, dev});
-    g_pending.insert(key);
-    if (!b.worker.joinable()) b.worker = std::thread([] { b.run(); });
-    g_cv.notify_all();
-}
-
 template <typename T, typename FC>
 struct JArgs {
     long long n;
@@ -279,34 +214,20 @@ struct JArgs {
 template <typename T, typename FC>
 bool launch_impl(const Prog &p, const T *const *hi, const T *const *lo, T *oh, T *ol, uint8_t *fl, const FC &fc,
                  int64_t n, cudaStream_t stream, int *status) {
-    cudaKernel_t k = nullptr;
+    cudaKernel_t k;
     {
-        std::unique_lock<std::mutex> g(g_mu);
+        std::lock_guard<std::mutex> g(g_mu);
         const int m = mode_locked();
         if (m == 0 || (m == 1 && n < kAutoMinElements)) return false;
         const std::string key = key_of(p);
         auto it = g_cache.find(key);
-        if (it != g_cache.end()) {
-            k = it->second;
-        } else if (m == 1) {
-            // automatic: build in the background, run generic until it is done
-            if (!g_pending.count(key)) enqueue_locked(key, p);
-            return false;
+        if (it == g_cache.end()) {
+            k = build(p);
+            g_cache.emplace(key, k);
+            if (k) ++g_built;
+            else ++g_failed;
         } else {
-            // mode 2: the specialised kernel now (after a background build of
-            // the same program, if one is running)
-            if (g_pending.count(key)) {
-                g_cv.wait_for(g, std::chrono::seconds(120), [&] { return !g_pending.count(key); });
-                it = g_cache.find(key);
-                if (it == g_cache.end()) return false;
-                k = it->second;
-            } else {
-                g_pending.insert(key);
-                g.unlock();
-                k = build(p);
-                g.lock();
-                finish_locked(key, k);
-            }
+            k = it->second;
         }
     }
     if (!k) return false;
@@ -348,14 +269,6 @@ bool launch(const Prog &p, const float *const *hi, const float *const *lo, float
 }
 
 }  // namespace tfjit
-
-extern "C" int twofold_ew_jit_wait(int64_t timeout_ms) {
-    std::unique_lock<std::mutex> g(tfjit::g_mu);
-    const int64_t ms = timeout_ms < 0 ? 60000 : timeout_ms;
-    return tfjit::g_cv.wait_for(g, std::chrono::milliseconds(ms), [] { return tfjit::g_pending.empty(); })
-               ? TF_OK
-               : TF_ETIMEOUT;
-}
 
 extern "C" int twofold_ew_jit(int32_t mode, int64_t *built, int64_t *failed) {
     std::lock_guard<std::mutex> g(tfjit::g_mu);

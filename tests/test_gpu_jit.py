@@ -86,9 +86,8 @@ def test_forced_specialisation_binary32(n):
 
 
 def test_automatic_mode_builds_once_per_program():
-    """n >= 2^20 specialises: the first call starts one background build and
-    runs on the generic kernels, the next call runs the built kernel with the
-    same bits; the results equal the oracle (sampled) and a small call of the
+    """n >= 2^20 specialises; the second call of the same program reuses the
+    kernel; the results equal the oracle (sampled) and a small call of the
     same program stays generic."""
     T.jit_mode(1)
     n = (1 << 20) + 3
@@ -96,15 +95,11 @@ def test_automatic_mode_builds_once_per_program():
     g = [(dev(d[k + "0"]), dev(d[k + "1"])) for k in "abcd"]
     prog = [(O.MUL, 4, 0, 1), (O.SUB, 5, 4, 2), (O.DIV, 6, 5, 3), (O.SQRT, 7, 6, 6), (O.ADD, 8, 7, 7)]
     _, b0, _ = T.jit_mode(-1)
-    z0, z1, fl = T.twofold_ew(prog, g)          # starts the build; runs on the generic kernels
-    assert T.jit_wait(120000)
+    z0, z1, fl = T.twofold_ew(prog, g)
     _, b1, _ = T.jit_mode(-1)
-    y0, y1, yf = T.twofold_ew(prog, g)          # the specialised kernel
+    T.twofold_ew(prog, g)
     _, b2, f2 = T.jit_mode(-1)
     assert b1 == b0 + 1 and b2 == b1 and f2 == 0
-    assert_bits(host(y0), host(z0), "specialised z0 = generic z0")
-    assert_bits(host(y1), host(z1), "specialised z1 = generic z1")
-    assert_flags(host(yf), host(fl), "specialised flags = generic flags")
     idx = np.r_[0:5000, n - 5000:n]
     ins = [(d[k + "0"][idx], d[k + "1"][idx]) for k in "abcd"]
     r0, r1, rf = O.ew(prog, ins)
