@@ -30,9 +30,11 @@ namespace {
 
 constexpr int kThreads = 128;
 
-// binary32 is bandwidth-bound: two elements per thread, all loads first;
-// binary64 is bound by its arithmetic: one element per thread, more threads.
-int elems_of(const Prog &p) { return p.is_f32 ? 2 : 1; }
+// binary32 is bandwidth-bound: two elements per thread, all loads first
+// (four consecutive ones in 16-byte accesses when the arrays allow: the
+// twofold chain 1.80 -> 1.64 ms at 2^28, 90 -> 98 % of HBM); binary64 is
+// bound by its arithmetic: one element per thread, more threads.
+int elems_of(const Prog &p) { return p.vec4 ? 4 : (p.is_f32 ? 2 : 1); }
 
 std::mutex g_mu;
 std::unordered_map<std::string, cudaKernel_t> g_cache;     // nullptr: failed to build
@@ -50,8 +52,8 @@ int mode_locked() {
 std::string key_of(const Prog &p) {
     std::string k(p.is_f32 ? "f" : "d");
     char buf[64];
-    std::snprintf(buf, sizeof buf, "|%d|%d|%x|%d|%d|%d%d|", p.nprog, p.nin, p.dotted_mask, p.flags ? 1 : 0,
-                  p.sticky ? 1 : 0, p.plain ? 1 : 0, p.plain_int ? 1 : 0);
+    std::snprintf(buf, sizeof buf, "|%d|%d|%x|%d|%d|%d%d%d|", p.nprog, p.nin, p.dotted_mask, p.flags ? 1 : 0,
+                  p.sticky ? 1 : 0, p.plain ? 1 : 0, p.plain_int ? 1 : 0, p.vec4 ? 1 : 0);
     k += buf;
     for (int s = 0; s < p.nprog; ++s) {
         std::snprintf(buf, sizeof buf, "%d,%d,%d,%d;", p.op[s], p.dst[s], p.a[s], p.b[s]);
@@ -68,10 +70,94 @@ bool unary(int op) { return op == TF_SQRT || op == TF_PSQRT; }
 // registers, a little spill to L1: 3.6 % faster than 12); longer programs
 // keep 12 (40 registers).  binary32 (two elements per thread): the twofold
 // kernel at 8 (1.80 ms against 1.83 with the compiler's choice, 1.91 at
-// 12), the plain twin at 16 (0.85 ms against 0.97).
+// 12), the plain twin at 16 (0.85 ms against 0.97); with four elements per
+// thread at 6 (1.641 ms against 1.647 at 8).
 std::string min_blocks(const Prog &p) {
+    if (p.vec4) return ", 6";
     if (p.is_f32) return p.plain ? ", 16" : ", 8";
     return p.nin <= 4 && p.nprog <= 8 ? ", 16" : ", 12";
+}
+
+// The binary32 twofold kernel with four consecutive elements per thread:
+// each input's heads and tails as one 16-byte load, the results as 16-byte
+// stores and the flags as one 4-byte store; the last partial group of the
+// array through scalar accesses.
+std::string source_vec4(const Prog &p, const bool *used, const bool *written, bool coupled) {
+    std::string s = std::string("extern \"C\" __global__ void __launch_bounds__(128") + min_blocks(p) +
+                    ") tf_jit_ew(const __grid_constant__ JArgs A) {\n";
+    s += "  for (long long j = (long long)blockIdx.x * 128 + threadIdx.x; 4 * j < A.n; j += (long long)gridDim.x * 128) {\n";
+    s += "    const long long i0 = 4 * j; const bool full = i0 + 3 < A.n;\n";
+    char buf[1024];
+    for (int k = 0; k < p.nin; ++k) {
+        if (!used[k]) continue;
+        const bool dotted = (p.dotted_mask >> k) & 1;
+        std::snprintf(buf, sizeof buf,
+                      "    float4 h%d, l%d = make_float4(0.f, 0.f, 0.f, 0.f);\n"
+                      "    if (full) h%d = *reinterpret_cast<const float4 *>(A.hi[%d] + i0);\n"
+                      "    else { h%d = make_float4(A.hi[%d][i0], i0 + 1 < A.n ? A.hi[%d][i0 + 1] : 1.f, "
+                      "i0 + 2 < A.n ? A.hi[%d][i0 + 2] : 1.f, 1.f); }\n",
+                      k, k, k, k, k, k, k, k);
+        s += buf;
+        if (!dotted) {
+            std::snprintf(buf, sizeof buf,
+                          "    if (full) l%d = *reinterpret_cast<const float4 *>(A.lo[%d] + i0);\n"
+                          "    else { l%d = make_float4(A.lo[%d][i0], i0 + 1 < A.n ? A.lo[%d][i0 + 1] : 0.f, "
+                          "i0 + 2 < A.n ? A.lo[%d][i0 + 2] : 0.f, 0.f); }\n",
+                          k, k, k, k, k, k);
+            s += buf;
+        }
+    }
+    static const char *const comp[4] = {"x", "y", "z", "w"};
+    const int last = p.dst[p.nprog - 1];
+    s += "    float r0[4], r1[4];\n    unsigned char fo[4] = {0, 0, 0, 0};\n";
+    for (int e = 0; e < 4; ++e) {
+        s += "    {\n      unsigned char st = 0;\n";
+        for (int k = 0; k < p.nin; ++k) {
+            if (!used[k]) continue;
+            std::snprintf(buf, sizeof buf, "      T e%dr%d_0 = h%d.%s, e%dr%d_1 = l%d.%s;\n", e, k, k, comp[e], e, k,
+                          k, comp[e]);
+            s += buf;
+        }
+        for (int r = p.nin; r < TF_EW_MAX_REGS; ++r)
+            if (written[r]) {
+                std::snprintf(buf, sizeof buf, "      T e%dr%d_0, e%dr%d_1;\n", e, r, e, r);
+                s += buf;
+            }
+        for (int q = 0; q < p.nprog; ++q) {
+            const int op = p.op[q], a = p.a[q], b = p.b[q], d = p.dst[q];
+            const bool xd = a < p.nin && ((p.dotted_mask >> a) & 1);
+            const bool yd = unary(op) || (b < p.nin && ((p.dotted_mask >> b) & 1));
+            std::string y0 = "T(0)", y1 = "T(0)";
+            if (!unary(op)) {
+                y0 = "e" + std::to_string(e) + "r" + std::to_string(b) + "_0";
+                y1 = "e" + std::to_string(e) + "r" + std::to_string(b) + "_1";
+            }
+            std::snprintf(buf, sizeof buf,
+                          "      { const tf::f2 z = tf::apply_any<%s>(%d, e%dr%d_0, e%dr%d_1, %s, %s, %s, %s); "
+                          "e%dr%d_0 = z.z0; e%dr%d_1 = z.z1;%s }\n",
+                          coupled ? "true" : "false", op, e, a, e, a, xd ? "true" : "false", y0.c_str(),
+                          y1.c_str(), yd ? "true" : "false", e, d, e, d,
+                          p.sticky ? " st |= tf::flag_of(z.z0, z.z1, A.fc);" : "");
+            s += buf;
+        }
+        std::snprintf(buf, sizeof buf, "      r0[%d] = e%dr%d_0; r1[%d] = e%dr%d_1;\n", e, e, last, e, e, last);
+        s += buf;
+        if (p.flags) {
+            std::snprintf(buf, sizeof buf, "      fo[%d] = tf::flag_of(e%dr%d_0, e%dr%d_1, A.fc) | st;\n", e, e,
+                          last, e, last);
+            s += buf;
+        }
+        s += "      (void)st;\n    }\n";
+    }
+    s += "    if (full) {\n"
+         "      *reinterpret_cast<float4 *>(A.oh + i0) = make_float4(r0[0], r0[1], r0[2], r0[3]);\n"
+         "      *reinterpret_cast<float4 *>(A.ol + i0) = make_float4(r1[0], r1[1], r1[2], r1[3]);\n";
+    if (p.flags) s += "      *reinterpret_cast<uchar4 *>(A.fl + i0) = make_uchar4(fo[0], fo[1], fo[2], fo[3]);\n";
+    s += "    } else {\n      for (int e = 0; e < 4 && i0 + e < A.n; ++e) {\n        A.oh[i0 + e] = r0[e];\n"
+         "        A.ol[i0 + e] = r1[e];\n";
+    if (p.flags) s += "        A.fl[i0 + e] = fo[e];\n";
+    s += "      }\n    }\n  }\n}\n";
+    return s;
 }
 
 // Source of the specialised kernel.
@@ -93,6 +179,7 @@ std::string source_of(const Prog &p) {
     s += std::string("typedef ") + (p.is_f32 ? "tf::FlagCfg32" : "tf::FlagCfg") + " FC;\n";
     s += "struct JArgs { long long n; const T *hi[12]; const T *lo[12]; T *oh; T *ol; unsigned char *fl; FC fc; };\n";
     const int E = elems_of(p);
+    if (p.vec4) return s + source_vec4(p, used, written, coupled);
     s += std::string("extern \"C\" __global__ void __launch_bounds__(128") + min_blocks(p) + ") " +
          (p.plain ? "tf_jit_plain" : "tf_jit_ew") + "(const __grid_constant__ JArgs A) {\n";
     s += "  for (long long i0 = (long long)blockIdx.x * " + std::to_string(128 * E) +
@@ -212,8 +299,20 @@ struct JArgs {
 };
 
 template <typename T, typename FC>
-bool launch_impl(const Prog &p, const T *const *hi, const T *const *lo, T *oh, T *ol, uint8_t *fl, const FC &fc,
+bool launch_impl(const Prog &p_in, const T *const *hi, const T *const *lo, T *oh, T *ol, uint8_t *fl, const FC &fc,
                  int64_t n, cudaStream_t stream, int *status) {
+    Prog p = p_in;
+    p.vec4 = false;
+    if (p.is_f32 && !p.plain) {
+        // four consecutive elements per thread when every array is 16-byte
+        // aligned (the flags 4-byte aligned)
+        uintptr_t m = reinterpret_cast<uintptr_t>(oh) | reinterpret_cast<uintptr_t>(ol);
+        for (int i = 0; i < p.nin; ++i) {
+            m |= reinterpret_cast<uintptr_t>(hi[i]);
+            if (!((p.dotted_mask >> i) & 1)) m |= reinterpret_cast<uintptr_t>(lo[i]);
+        }
+        p.vec4 = (m & 15) == 0 && (!p.flags || (reinterpret_cast<uintptr_t>(fl) & 3) == 0);
+    }
     cudaKernel_t k;
     {
         std::lock_guard<std::mutex> g(g_mu);

@@ -20,6 +20,8 @@ struct Prog {
     bool flags, sticky, is_f32;
     bool plain;                 // the plain twin: heads only, one output
     bool plain_int;             // plain twin: division and root on the integer pipes
+    bool vec4;                  // binary32 twofold: four consecutive elements per thread in
+                                // 16-byte accesses (set at launch when every array allows it)
 };
 
 // Launches the program's specialised kernel and returns true (status: the

@@ -85,6 +85,38 @@ def test_forced_specialisation_binary32(n):
                       "plain twin")
 
 
+@pytest.mark.parametrize("shift,n", [(0, 4099), (1, 4099), (2, 4100), (0, 4096)])
+def test_binary32_four_element_path_and_unaligned_views(shift, n):
+    """The binary32 twofold kernel takes four consecutive elements per thread
+    in 16-byte accesses when every array is 16-byte aligned, with the last
+    partial group through scalar accesses; views that start 1 or 2 elements
+    into an allocation take the two-element kernel.  Both give the oracle's
+    bits."""
+    import torch
+    rng = np.random.default_rng(77 + shift + n)
+    ins = []
+    for k in range(4):
+        h = np.abs(rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 3, n)).astype(np.float32)
+        lo = None if k == 3 else (h * 2.0 ** -30 * rng.uniform(-1, 1, n)).astype(np.float32)
+        ins.append((h, lo))
+
+    def view(a):
+        if a is None:
+            return None
+        buf = torch.empty(n + 8, dtype=torch.float32, device="cuda")
+        buf[shift:shift + n].copy_(torch.from_numpy(a))
+        return buf[shift:shift + n]
+
+    prog = [(O.MUL, 4, 0, 1), (O.ADD, 5, 4, 2), (O.DIV, 6, 5, 3), (O.SQRT, 7, 6, 6)]
+    T.jit_mode(2)
+    p = T.params(panic_mode=O.REL, panic_tau=2.0 ** -18)
+    z0, z1, fl = T.twofold_ew_f32(prog, [(view(h), view(lo)) for h, lo in ins], p=p)
+    r0, r1, rf = O.ew32(prog, ins, mode=O.REL, tau=2.0 ** -18, m=2.0)
+    assert_bits32(z0, r0, f"shift {shift} n {n} z0")
+    assert_bits32(z1, r1, f"shift {shift} n {n} z1")
+    assert_flags(fl, rf, f"shift {shift} n {n} flags")
+
+
 def test_automatic_mode_builds_once_per_program():
     """n >= 2^20 specialises; the second call of the same program reuses the
     kernel; the results equal the oracle (sampled) and a small call of the
