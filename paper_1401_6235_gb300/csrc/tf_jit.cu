@@ -32,8 +32,9 @@ constexpr int kThreads = 128;
 
 // binary32 is bandwidth-bound: two elements per thread, all loads first
 // (four consecutive ones in 16-byte accesses when the arrays allow: the
-// twofold chain 1.80 -> 1.64 ms at 2^28, 90 -> 98 % of HBM); binary64 is
-// bound by its arithmetic: one element per thread, more threads.
+// twofold chain 1.80 -> 1.64 ms at 2^28, 90 -> 99 % of HBM, the plain twin
+// 0.85 -> 0.79 ms); binary64 is bound by its arithmetic: one element per
+// thread, more threads.
 int elems_of(const Prog &p) { return p.vec4 ? 4 : (p.is_f32 ? 2 : 1); }
 
 std::mutex g_mu;
@@ -71,9 +72,10 @@ bool unary(int op) { return op == TF_SQRT || op == TF_PSQRT; }
 // keep 12 (40 registers).  binary32 (two elements per thread): the twofold
 // kernel at 8 (1.80 ms against 1.83 with the compiler's choice, 1.91 at
 // 12), the plain twin at 16 (0.85 ms against 0.97); with four elements per
-// thread at 6 (1.641 ms against 1.647 at 8).
+// thread the twofold kernel at 6 (1.641 ms against 1.647 at 8), the plain
+// twin at 16 (0.793 ms against 0.799 at 12).
 std::string min_blocks(const Prog &p) {
-    if (p.vec4) return ", 6";
+    if (p.vec4) return p.plain ? ", 16" : ", 6";
     if (p.is_f32) return p.plain ? ", 16" : ", 8";
     return p.nin <= 4 && p.nprog <= 8 ? ", 16" : ", 12";
 }
@@ -83,14 +85,14 @@ std::string min_blocks(const Prog &p) {
 // stores and the flags as one 4-byte store; the last partial group of the
 // array through scalar accesses.
 std::string source_vec4(const Prog &p, const bool *used, const bool *written, bool coupled) {
-    std::string s = std::string("extern \"C\" __global__ void __launch_bounds__(128") + min_blocks(p) +
-                    ") tf_jit_ew(const __grid_constant__ JArgs A) {\n";
+    std::string s = std::string("extern \"C\" __global__ void __launch_bounds__(128") + min_blocks(p) + ") " +
+                    (p.plain ? "tf_jit_plain" : "tf_jit_ew") + "(const __grid_constant__ JArgs A) {\n";
     s += "  for (long long j = (long long)blockIdx.x * 128 + threadIdx.x; 4 * j < A.n; j += (long long)gridDim.x * 128) {\n";
     s += "    const long long i0 = 4 * j; const bool full = i0 + 3 < A.n;\n";
     char buf[1024];
     for (int k = 0; k < p.nin; ++k) {
         if (!used[k]) continue;
-        const bool dotted = (p.dotted_mask >> k) & 1;
+        const bool dotted = p.plain || ((p.dotted_mask >> k) & 1);
         std::snprintf(buf, sizeof buf,
                       "    float4 h%d, l%d = make_float4(0.f, 0.f, 0.f, 0.f);\n"
                       "    if (full) h%d = *reinterpret_cast<const float4 *>(A.hi[%d] + i0);\n"
@@ -125,6 +127,12 @@ std::string source_vec4(const Prog &p, const bool *used, const bool *written, bo
             }
         for (int q = 0; q < p.nprog; ++q) {
             const int op = p.op[q], a = p.a[q], b = p.b[q], d = p.dst[q];
+            if (p.plain) {                       // the plain twin: heads only
+                std::snprintf(buf, sizeof buf, "      e%dr%d_0 = tf::apply_plain(%d, e%dr%d_0, %s);\n", e, d, op, e, a,
+                              unary(op) ? "T(0)" : ("e" + std::to_string(e) + "r" + std::to_string(b) + "_0").c_str());
+                s += buf;
+                continue;
+            }
             const bool xd = a < p.nin && ((p.dotted_mask >> a) & 1);
             const bool yd = unary(op) || (b < p.nin && ((p.dotted_mask >> b) & 1));
             std::string y0 = "T(0)", y1 = "T(0)";
@@ -140,22 +148,24 @@ std::string source_vec4(const Prog &p, const bool *used, const bool *written, bo
                           p.sticky ? " st |= tf::flag_of(z.z0, z.z1, A.fc);" : "");
             s += buf;
         }
-        std::snprintf(buf, sizeof buf, "      r0[%d] = e%dr%d_0; r1[%d] = e%dr%d_1;\n", e, e, last, e, e, last);
+        std::snprintf(buf, sizeof buf, "      r0[%d] = e%dr%d_0; r1[%d] = %s;\n", e, e, last, e,
+                      p.plain ? "T(0)" : ("e" + std::to_string(e) + "r" + std::to_string(last) + "_1").c_str());
         s += buf;
-        if (p.flags) {
+        if (p.flags && !p.plain) {
             std::snprintf(buf, sizeof buf, "      fo[%d] = tf::flag_of(e%dr%d_0, e%dr%d_1, A.fc) | st;\n", e, e,
                           last, e, last);
             s += buf;
         }
         s += "      (void)st;\n    }\n";
     }
+    const bool twofold = !p.plain, fl = p.flags && !p.plain;
     s += "    if (full) {\n"
-         "      *reinterpret_cast<float4 *>(A.oh + i0) = make_float4(r0[0], r0[1], r0[2], r0[3]);\n"
-         "      *reinterpret_cast<float4 *>(A.ol + i0) = make_float4(r1[0], r1[1], r1[2], r1[3]);\n";
-    if (p.flags) s += "      *reinterpret_cast<uchar4 *>(A.fl + i0) = make_uchar4(fo[0], fo[1], fo[2], fo[3]);\n";
-    s += "    } else {\n      for (int e = 0; e < 4 && i0 + e < A.n; ++e) {\n        A.oh[i0 + e] = r0[e];\n"
-         "        A.ol[i0 + e] = r1[e];\n";
-    if (p.flags) s += "        A.fl[i0 + e] = fo[e];\n";
+         "      *reinterpret_cast<float4 *>(A.oh + i0) = make_float4(r0[0], r0[1], r0[2], r0[3]);\n";
+    if (twofold) s += "      *reinterpret_cast<float4 *>(A.ol + i0) = make_float4(r1[0], r1[1], r1[2], r1[3]);\n";
+    if (fl) s += "      *reinterpret_cast<uchar4 *>(A.fl + i0) = make_uchar4(fo[0], fo[1], fo[2], fo[3]);\n";
+    s += "    } else {\n      for (int e = 0; e < 4 && i0 + e < A.n; ++e) {\n        A.oh[i0 + e] = r0[e];\n";
+    if (twofold) s += "        A.ol[i0 + e] = r1[e];\n";
+    if (fl) s += "        A.fl[i0 + e] = fo[e];\n";
     s += "      }\n    }\n  }\n}\n";
     return s;
 }
@@ -303,15 +313,16 @@ bool launch_impl(const Prog &p_in, const T *const *hi, const T *const *lo, T *oh
                  int64_t n, cudaStream_t stream, int *status) {
     Prog p = p_in;
     p.vec4 = false;
-    if (p.is_f32 && !p.plain) {
+    if (p.is_f32) {
         // four consecutive elements per thread when every array is 16-byte
         // aligned (the flags 4-byte aligned)
-        uintptr_t m = reinterpret_cast<uintptr_t>(oh) | reinterpret_cast<uintptr_t>(ol);
+        uintptr_t m = reinterpret_cast<uintptr_t>(oh);
+        if (!p.plain) m |= reinterpret_cast<uintptr_t>(ol);
         for (int i = 0; i < p.nin; ++i) {
             m |= reinterpret_cast<uintptr_t>(hi[i]);
-            if (!((p.dotted_mask >> i) & 1)) m |= reinterpret_cast<uintptr_t>(lo[i]);
+            if (!p.plain && !((p.dotted_mask >> i) & 1)) m |= reinterpret_cast<uintptr_t>(lo[i]);
         }
-        p.vec4 = (m & 15) == 0 && (!p.flags || (reinterpret_cast<uintptr_t>(fl) & 3) == 0);
+        p.vec4 = (m & 15) == 0 && (p.plain || !p.flags || (reinterpret_cast<uintptr_t>(fl) & 3) == 0);
     }
     cudaKernel_t k;
     {

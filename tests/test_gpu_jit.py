@@ -87,11 +87,11 @@ def test_forced_specialisation_binary32(n):
 
 @pytest.mark.parametrize("shift,n", [(0, 4099), (1, 4099), (2, 4100), (0, 4096)])
 def test_binary32_four_element_path_and_unaligned_views(shift, n):
-    """The binary32 twofold kernel takes four consecutive elements per thread
-    in 16-byte accesses when every array is 16-byte aligned, with the last
-    partial group through scalar accesses; views that start 1 or 2 elements
-    into an allocation take the two-element kernel.  Both give the oracle's
-    bits."""
+    """The binary32 kernels (twofold and plain twin) take four consecutive
+    elements per thread in 16-byte accesses when every array is 16-byte
+    aligned, with the last partial group through scalar accesses; views that
+    start 1 or 2 elements into an allocation take the two-element kernels.
+    All give the oracle's bits."""
     import torch
     rng = np.random.default_rng(77 + shift + n)
     ins = []
@@ -115,6 +115,8 @@ def test_binary32_four_element_path_and_unaligned_views(shift, n):
     assert_bits32(z0, r0, f"shift {shift} n {n} z0")
     assert_bits32(z1, r1, f"shift {shift} n {n} z1")
     assert_flags(fl, rf, f"shift {shift} n {n} flags")
+    assert_bits32(T.plain_ew_f32(prog, [view(h) for h, _ in ins]), O.ew32_plain(prog, [h for h, _ in ins]),
+                  f"shift {shift} n {n} plain twin")
 
 
 def test_automatic_mode_builds_once_per_program():
