@@ -497,6 +497,16 @@ __device__ __forceinline__ unsigned cluster_rank() {
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// The same meeting without memory ordering: for the end of the pair kernel,
+// where only the order of execution matters (the consumer arrives after its
+// mbarriers completed, so no copy still reads the producer's shared memory;
+// the partials reach the final tree through the grid's completion).  The
+// release form made the consumer wait for its global stores first (~0.5 us
+// per call).
+__device__ __forceinline__ void cluster_sync_exec() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+}
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint32_t peer_addr(uint32_t a, unsigned rank) {
     uint32_t r;
@@ -808,7 +818,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
             else { A.part0[b] = acc.z0; A.part1[b] = acc.z1; }
         }
     }
-    cluster_sync_all();
+    cluster_sync_exec();
 }
 
 // Leaves per pair: the largest power of two <= 32 with B L <= kLatElems that
