@@ -497,12 +497,15 @@ __device__ __forceinline__ unsigned cluster_rank() {
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// The same meeting without memory ordering: for the end of the pair kernel,
-// where only the order of execution matters (the consumer arrives after its
-// mbarriers completed, so no copy still reads the producer's shared memory;
-// the partials reach the final tree through the grid's completion).  The
-// release form made the consumer wait for its global stores first (~0.5 us
-// per call).
+// The same meeting with a relaxed arrive (the wait keeps its default
+// acquire): at the start of the pair kernel, after fence.mbarrier_init has
+// released the mbarriers' initialisation, and at its end, where only the
+// order of execution matters (the consumer arrives after its mbarriers
+// completed, so no copy still reads the producer's shared memory; the
+// partials reach the final tree through the grid's completion).  A release
+// arrive waits for the CTA's earlier memory accesses: at the end the
+// consumer's global stores (~0.5 us per call), at the start the terms'
+// loads in flight.
 __device__ __forceinline__ void cluster_sync_exec() {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
     asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
@@ -706,9 +709,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kLatThreads) reduce_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         mbar_expect(smem_addr(&mbar[t]), bytes);
     }
-    // the consumer's mbarriers are ready before any producer copy; the
-    // terms follow in both CTAs
-    cluster_sync_all();
+    // the consumer's mbarriers are ready before any producer copy (their
+    // initialisation is released by fence.mbarrier_init and acquired by the
+    // cluster wait; the arrive is relaxed so that the terms' loads stay in
+    // flight across the barrier); the terms follow in both CTAs
+    cluster_sync_exec();
     const int row = min(lane, nl - 1);
     {
         // terms: the producer keeps p_i = RN(x_i y_i) (or x_i for a sum),
